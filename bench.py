@@ -1,0 +1,357 @@
+"""Benchmark: FP64 SIPG operator throughput inside a Jacobi-PCG Poisson solve.
+
+Workload (one step): the pressure Poisson problem on the tanh-graded channel
+2 pi x 2 x pi with 32^3 cells, gamma = 1.8, periodic in x and z, Dirichlet
+walls, k = 4 (4,096,000 DoF); right-hand side b = M f_I with
+f = (5 + pi^2/4) sin x cos(pi y/2) sin 2z at the nodes; Jacobi-preconditioned
+CG from x = 0 to a relative residual of 1e-10, one CUDA graph per 16
+iterations.  The step is the whole solve.
+
+metric value = (applies in the solve) x n_dofs / (solve time): the FP64 SIPG
+operator applies in DoF/s sustained over the whole solve (CG vector updates and
+reductions included); ms_per_step is the time to the 1e-10 solve.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 it runs under torchrun, one independent replica of the workload per
+GPU (the path has no data exchange on one mesh per GPU: "replicas only").
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF/s of SIPG operator apply (FP64, FP32) and % HBM roofline; time to 1e-10 Poisson solve"
+UNIT = "DoF/s"
+WORKLOAD = dict(n=(32, 32, 32), lo=(0.0, -1.0, 0.0), hi=(2 * math.pi, 1.0, math.pi),
+                bc_lo=("periodic", "dirichlet", "periodic"), bc_hi=("periodic", "dirichlet", "periodic"),
+                mapping="channel", gamma=1.8, k=4)
+RTOL = 1e-10
+CHECK_EVERY = 16
+
+
+def fma_per_dof(p):
+    """FMAs per DoF of one Laplace apply in the Kronecker-sum evaluation (interior
+    faces): three line operators (p^2 + 6p per line: 1D stiffness, two faces with
+    own and neighbour normal derivative and the derivative scatter), five 1D mass
+    contractions (p^2 each) -> 8p + 18 per DoF."""
+    return 8 * p + 18
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != n_gpus and world > 1:
+        raise SystemExit("WORLD_SIZE %d != --gpus %d" % (world, n_gpus))
+    return rank, world, local
+
+
+def manufactured_f(X):
+    """f = -Laplace(u) for u = sin x cos(pi y/2) sin 2z, at the given points (n, 3)."""
+    import numpy as np
+    return (5 + math.pi ** 2 / 4) * np.sin(X[:, 0]) * np.cos(math.pi * X[:, 1] / 2) * np.sin(2 * X[:, 2])
+
+
+def cpu_baseline(max_seconds=25.0):
+    """The oracle as it stands (dense-quadrature element-by-element FP64 apply
+    inside its textbook Jacobi-PCG) on the same 32^3 k=4 channel problem, run
+    for a bounded number of CG iterations; returns the same metric."""
+    import numpy as np
+    from oracle.mesh import MeshSpec
+    from oracle.sipg import SIPG
+    from oracle import solvers
+    w = WORKLOAD
+    spec = MeshSpec(*w["n"], lo=w["lo"], hi=w["hi"], bc_lo=w["bc_lo"], bc_hi=w["bc_hi"], mapping=w["mapping"],
+                    gamma=w["gamma"])
+    t0 = time.time()
+    op = SIPG(spec, w["k"])
+    setup = time.time() - t0
+    X = op.node_coordinates().reshape(-1, 3)
+    b = op.mass_apply(manufactured_f(X))
+    d = op.diagonal()
+    n = b.size
+    napply = [0]
+
+    def A(v):
+        napply[0] += 1
+        return op.apply(v)
+
+    c0, t0 = time.process_time(), time.time()
+    iters = 1
+    while True:
+        napply[0] = 0
+        c0, t0 = time.process_time(), time.time()
+        solvers.cg(A, b, rtol=0.0, maxit=iters, precond=lambda r: r / d)
+        wall = time.time() - t0
+        if wall * 2 > max_seconds or iters >= 64:
+            break
+        iters *= 2
+    cpu = time.process_time() - c0
+    value = napply[0] * n / wall
+    cores = max(1, round(cpu / wall))
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d oracle Jacobi-PCG iterations (%d FP64 applies) of the 32^3 k=4 channel Poisson problem, "
+                      "%.1f s wall after %.1f s setup; DoF-applies per second" % (iters, napply[0], wall, setup),
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(max_seconds=20.0 if i >= args.warmup else 5.0)
+        if i >= args.warmup:
+            steps.append(cb)
+    value = statistics.median(s["value"] for s in steps)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "poisson_channel_32x32x32_k4_jacobi_pcg_1e-10", "dofs": 4096000},
+            "cpu_baseline": dict(steps[-1], value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1607_01323_gb300 import Mesh, apply_laplace_f32, apply_laplace_f64, apply_mass_f64, cg_solve
+    from paper_1607_01323_gb300 import _lib as L
+    import ctypes as C
+
+    w = WORKLOAD
+    m = Mesh(w["n"], w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"], k=w["k"])
+    N = m.n_dofs
+    p = w["k"] + 1
+    X = m.node_coordinates()
+    b = apply_mass_f64(m, torch.tensor(manufactured_f(X), device="cuda"))
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    opts = dict(precond="jacobi", rtol=RTOL, use_graph=1, check_every=CHECK_EVERY)
+
+    def solve():
+        x.zero_()
+        return cg_solve(m, b, x, **opts)[1]
+
+    for _ in range(args.warmup):
+        res = solve()
+    torch.cuda.synchronize()
+    m.profile_enable(True)
+    m.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    iters = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        res = solve()
+        ev[i][1].record()
+        iters.append(res.iters)
+        if not res.converged:
+            raise SystemExit("solve did not converge: %r" % res)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    apply_ms, applies, launches = m.profile_read(reset=True)
+    m.profile_enable(False)
+    t_steps = [a.elapsed_time(bb) for a, bb in ev]
+    t_total = sum(t_steps) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = tt.item()
+    n_applies = sum(it + 1 for it in iters)  # initial residual + one per iteration
+    value = world * n_applies * N / t_total
+    ms_per_step = 1e3 * t_total / args.steps
+
+    # end to end through the public API: pinned host rhs -> device, solve, solution -> host
+    hb = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    hb.copy_(b.cpu())
+    hx = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    db = torch.empty_like(b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_iters = 0
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0.record()
+        db.copy_(hb, non_blocking=True)
+        x.zero_()
+        _, r2 = cg_solve(m, db, x, **opts)
+        hx.copy_(x, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_iters += r2.iters + 1
+    e2e_value = world * e2e_iters * N / (e2e_ms / 1e3)
+
+    # FP32 operator apply throughput on the same mesh (outside the timed step)
+    x32 = b.float()
+    y32 = torch.empty_like(x32)
+    for _ in range(3):
+        apply_laplace_f32(m, x32, y32)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    f32_ms = 0.0
+    for i in range(reps):
+        flush.fill_(float(i))
+        f0.record()
+        apply_laplace_f32(m, x32, y32)
+        f1.record()
+        torch.cuda.synchronize()
+        f32_ms += f0.elapsed_time(f1)
+    f32_ms /= reps
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs")
+    avg_apply_ms = apply_ms / max(applies, 1)
+    flops = 2.0 * fma_per_dof(p) * N
+    achieved_tflops = flops / (avg_apply_ms / 1e3) / 1e12
+    # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    bytes_apply = 16.0 * N  # read x, write y (FP64)
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic_apply_f64_channel32_k4.json")
+    if os.path.exists(tf):
+        with open(tf) as f:
+            traffic = json.load(f).get("dram_bytes_per_launch")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "poisson_channel_32x32x32_k4_jacobi_pcg_1e-10", "dofs": N, "k": w["k"],
+                   "gamma": w["gamma"], "rtol": RTOL, "cg_iters": iters[-1], "cuda_graph_chunk": CHECK_EVERY,
+                   "l2": "256 MB buffer written between timed steps (outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "time_to_solve_s": ms_per_step / 1e3,
+        "apply_f64": {"avg_ms": avg_apply_ms, "dofs_per_s": N / (avg_apply_ms / 1e3), "timed_launches": applies,
+                      "hbm_frac": (bytes_apply / (avg_apply_ms / 1e3) / 1e9) / hbm if hbm else None},
+        "apply_f32": {"avg_ms": f32_ms, "dofs_per_s": N / (f32_ms / 1e3),
+                      "hbm_frac": (8.0 * N / (f32_ms / 1e3) / 1e9) / hbm if hbm else None,
+                      "note": "separate timing of the FP32 operator on the same mesh, L2 flushed per launch"},
+        "roofline": {"bound": "alu", "kernel": "apply_kernel<double,5>", "achieved": achieved_tflops,
+                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved_tflops / fp64_peak,
+                     "traffic": traffic, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 x 2.07 GHz",
+                     "flops_per_dof": 2 * fma_per_dof(p),
+                     "hbm": {"achieved_gbs": bytes_apply / (avg_apply_ms / 1e3) / 1e9, "peak_gbs": hbm,
+                             "frac": (bytes_apply / (avg_apply_ms / 1e3) / 1e9) / hbm if hbm else None,
+                             "bytes_per_dof": 16}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * sipg.h -- C ABI of the GB300 matrix-free SIPG library (libsipg.so).
+ *
+ * Method: Krank, Fehn, Wall, Kronbichler, "A high-order semi-explicit
+ * discontinuous Galerkin solver for 3D incompressible flow with application to
+ * DNS and LES of turbulent channel flow" (arXiv:1607.01323).  The library
+ * evaluates, matrix-free and by sum factorisation (Sec. 5), the symmetric
+ * interior-penalty operators that the paper's conjugate-gradient solvers apply
+ * at every iteration (Sec. 5.1):
+ *   - the pressure Poisson operator L of Sec. 3.2 (ii) (fluxes P*, Pi*,
+ *     penalty of Eq. (taue) with the max rule of Eq. (tau)), Eq. (poissonmat);
+ *   - the viscous Helmholtz operator (gamma0/dt) M - F^nu of Eq. (viscous), in
+ *     Laplace form (gamma0/dt) M + nu L per velocity component;
+ *   - the tensorial inverse mass matrix (Sec. 5);
+ * plus the Jacobi / inverse-mass / FP32-Chebyshev preconditioned CG of
+ * Sec. 5.1 and an adjoint gradient with respect to a per-cell viscosity.
+ *
+ * Discretisation: Q_k on hexahedra with nodal Lagrange polynomials on the
+ * Gauss-Lobatto points (Sec. 3.1), Gauss quadrature with k+1 points per
+ * direction (Sec. 5), iso-parametric degree-k mapping (Sec. 5).  Meshes are
+ * structured boxes of nx x ny x nz cells whose map is separable per direction:
+ * affine, or affine in x and z with the tanh wall-normal grading of Sec. 7.1.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status (sipg_status) and never aborts,
+ *     traps or exits; sipg_last_error() returns a thread-local message for the
+ *     last failure on the calling thread.
+ *   - Host arguments are validated before any work: NULL pointers, ranges,
+ *     sizes.  CUDA errors map to SIPG_ECUDA.
+ *   - Vector layout: x[comp][cell][c][b][a], a along x fastest, cells
+ *     numbered cell = (iz * ny + iy) * nx + ix; n_dofs = ncell * (k+1)^3 per
+ *     component.  Vectors are contiguous DEVICE pointers owned by the caller,
+ *     on the device that was current when the mesh was created; the library
+ *     never frees them.  x and y must not overlap.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  The apply
+ *     entry points are asynchronous on that stream; sipg_cg_solve returns
+ *     after the solve has finished (it reads convergence data to the host).
+ *   - A sipg_mesh is not thread-safe: do not use one mesh from two host
+ *     threads at the same time.
+ */
+#ifndef SIPG_H
+#define SIPG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sipg_mesh sipg_mesh; /* opaque, owned by the library */
+
+typedef enum {
+  SIPG_OK = 0,
+  SIPG_MAXITER = 1,       /* solver stopped at maxit without reaching rtol     */
+  SIPG_EINVAL = -1,       /* invalid argument (see sipg_last_error)             */
+  SIPG_ECUDA = -2,        /* a CUDA runtime call failed                        */
+  SIPG_ENOMEM = -3,       /* device or host allocation failed                  */
+  SIPG_BREAKDOWN = -4,    /* CG breakdown: p^T A p <= 0 or not finite          */
+  SIPG_NONFINITE = -5     /* right-hand side or residual not finite            */
+} sipg_status;
+
+typedef enum { SIPG_BC_PERIODIC = 0, SIPG_BC_DIRICHLET = 1, SIPG_BC_NEUMANN = 2 } sipg_bc;
+typedef enum { SIPG_MAP_AFFINE = 0, SIPG_MAP_CHANNEL_TANH = 1 } sipg_map;
+typedef enum { SIPG_OP_LAPLACE = 0, SIPG_OP_HELMHOLTZ = 1 } sipg_op;
+typedef enum {
+  SIPG_PC_NONE = 0,
+  SIPG_PC_JACOBI = 1,     /* z = diag(A)^-1 r (Sec. 5.1: the diagonal computed once)   */
+  SIPG_PC_INVMASS = 2,    /* z = M^-1 r (Sec. 5.1: viscous solver preconditioner)       */
+  SIPG_PC_CHEB_F32 = 3    /* Chebyshev in FP32 with the FP32 operator (Sec. 5.1)         */
+} sipg_precond;
+
+/* Mesh description.  "Dirichlet" is the side where the unknown is prescribed
+ * (homogeneous data): the SIPG boundary terms with penalty 2 tau (Sec. 3.2 (ii),
+ * pressure on dOmega^N; Sec. 3.2 (iii), velocity on dOmega^D).  "Neumann" sides
+ * carry no operator term.  Periodic sides must be paired (lo and hi) and are
+ * treated as interior faces.  map = SIPG_MAP_CHANNEL_TANH maps the global
+ * wall-normal coordinate eta in [0,1] to
+ *   y = lo[1] + (hi[1]-lo[1]) (1 + tanh(gamma (2 eta - 1)) / tanh(gamma)) / 2
+ * (Sec. 7.1 with delta = 1 for lo=-1, hi=1); x and z stay affine. */
+typedef struct {
+  int n[3];          /* cells per direction, each >= 1                         */
+  double lo[3];      /* box corner                                             */
+  double hi[3];      /* box corner, hi > lo                                    */
+  int bc_lo[3];      /* sipg_bc per side                                       */
+  int bc_hi[3];
+  int map;           /* sipg_map                                               */
+  double gamma;      /* grading parameter (> 0) for SIPG_MAP_CHANNEL_TANH       */
+} sipg_mesh_desc;
+
+/* Create a mesh on the current CUDA device.  The degree defaults to k = 3 and
+ * the penalty factor to 1; geometry tables are built on the device.
+ * Errors: EINVAL (bad description, unpaired periodic sides), ENOMEM, ECUDA. */
+int sipg_create_mesh(const sipg_mesh_desc* desc, sipg_mesh** out);
+
+/* Free the mesh and its device tables.  NULL is accepted.  Synchronises the
+ * device first so that no launch still reads the tables. */
+int sipg_destroy_mesh(sipg_mesh* mesh);
+
+/* Polynomial degree 1 <= k <= 7 of the nodal GLL basis (Sec. 3.1); rebuilds
+ * the 1D tables: Gauss rule with k+1 points (Sec. 5), iso-parametric
+ * degree-k interpolation of the map (Sec. 5), per-layer mass / stiffness /
+ * inverse-mass matrices, face derivative vectors and penalty terms. */
+int sipg_set_degree(sipg_mesh* mesh, int k);
+
+/* tau = factor * tau_IP of Eq. (taue) (factor > 0; default 1).  factor = 1/3
+ * gives (k+1)^2/h on interior cubes. */
+int sipg_set_penalty(sipg_mesh* mesh, double factor);
+
+/* Scalar DoFs per component: ncell * (k+1)^3 (host output). */
+int sipg_n_dofs(const sipg_mesh* mesh, long long* n);
+
+/* Number of cells (host output). */
+int sipg_n_cells(const sipg_mesh* mesh, long long* n);
+
+/* Physical coordinates of the nodal points: xyz[3 * i + d] for DoF i of one
+ * component (HOST buffer of 3 * n_dofs doubles, caller-owned). */
+int sipg_node_coordinates(const sipg_mesh* mesh, double* xyz_host);
+
+/* Per-cell penalty tau_e of Eq. (taue) times the penalty factor (HOST buffer of
+ * ncell doubles, caller-owned). */
+int sipg_penalty_values(const sipg_mesh* mesh, double* tau_host);
+
+/* y = L x: the SIPG Laplacian of Sec. 3.2 (ii) / Eq. (poissonmat), applied to
+ * ncomp >= 1 independent components (Sec. 5, sum factorisation). */
+int sipg_apply_laplace_f64(const sipg_mesh* mesh, const double* x, double* y, int ncomp, void* stream);
+int sipg_apply_laplace_f32(const sipg_mesh* mesh, const float* x, float* y, int ncomp, void* stream);
+
+/* y = mass_coef M x + nu L x, the viscous operator of Eq. (viscous) in
+ * Laplace form (mass_coef = gamma0/dt >= 0).  If nu_cell (DEVICE, ncell
+ * values > 0) is not NULL it replaces nu cell by cell: consistency terms use
+ * the average of nu grad u, the penalty max(nu-, nu+) (the paper has constant
+ * nu only). */
+int sipg_apply_helmholtz_f64(const sipg_mesh* mesh, double mass_coef, double nu, const double* nu_cell,
+                             const double* x, double* y, int ncomp, void* stream);
+int sipg_apply_helmholtz_f32(const sipg_mesh* mesh, float mass_coef, float nu, const float* nu_cell,
+                             const float* x, float* y, int ncomp, void* stream);
+
+/* y = M x, the block-diagonal mass matrix with the Gauss (k+1) rule (Sec. 4.4). */
+int sipg_apply_mass_f64(const sipg_mesh* mesh, const double* x, double* y, int ncomp, void* stream);
+
+/* y = M^-1 x, the tensorial inverse mass matrix of Sec. 5: with n_q = k+1 the
+ * 1D node-to-quadrature matrices are square and are inverted individually. */
+int sipg_apply_inverse_mass_f64(const sipg_mesh* mesh, const double* x, double* y, int ncomp, void* stream);
+
+/* diag(A) for op = SIPG_OP_LAPLACE (mass_coef, nu, nu_cell ignored) or
+ * SIPG_OP_HELMHOLTZ; diag is a DEVICE buffer of n_dofs doubles (one component).
+ * Sec. 5.1: the matrix diagonal used by Jacobi and Chebyshev. */
+int sipg_diagonal_f64(const sipg_mesh* mesh, int op, double mass_coef, double nu, const double* nu_cell,
+                      double* diag, void* stream);
+
+/* Options of sipg_cg_solve. */
+typedef struct {
+  int op;                 /* sipg_op                                                       */
+  double mass_coef;       /* Helmholtz: gamma0/dt                                          */
+  double nu;              /* Helmholtz: viscosity (ignored when nu_cell != NULL)           */
+  const double* nu_cell;  /* Helmholtz: DEVICE [ncell] or NULL                              */
+  int precond;            /* sipg_precond                                                  */
+  int cheb_degree;        /* Chebyshev steps (>= 1); degree d uses d-1 operator products   */
+  double cheb_range;      /* lambda_min = lambda_max / cheb_range (> 1)                     */
+  double cheb_lmax;       /* > 0: use this lambda_max of D^-1 A; <= 0: estimate (Lanczos)   */
+  int cheb_lanczos_steps; /* CG steps of the estimate (>= 2)                                */
+  int zero_mean;          /* project b and every A p onto zero mean (Sec. 5.1)              */
+  double rtol;            /* stop when ||r||_2 <= rtol ||b||_2 (recursive residual)        */
+  int maxit;              /* >= 1                                                          */
+  int flexible;           /* Polak-Ribiere beta (always used with SIPG_PC_CHEB_F32)         */
+  int use_graph;          /* capture check_every iterations in one CUDA graph and replay it  */
+  int check_every;        /* iterations between host convergence checks (>= 1)             */
+} sipg_cg_opts;
+
+/* Fill opts with defaults: Laplace, Jacobi, rtol 1e-10, maxit 10000, Chebyshev
+ * degree 4, range 20, estimated lambda_max with 20 steps, graph on, checks
+ * every 16 iterations. */
+int sipg_cg_default_opts(sipg_cg_opts* opts);
+
+/* Solve A x = b by preconditioned CG (Sec. 5.1) with the matrix-free FP64
+ * operator.  b, x: DEVICE, ncomp * n_dofs doubles; x holds the initial guess
+ * on entry and the solution on return.  The ncomp components form one
+ * block-diagonal system (one CG, inner products over all components).
+ * iters_out / relres_out (HOST, may be NULL) receive the iteration count and
+ * ||r||/||b|| of the recursive residual.  Synchronous.  Returns SIPG_OK,
+ * SIPG_MAXITER, SIPG_BREAKDOWN, SIPG_NONFINITE or an error.  Workspace
+ * (5 vectors, plus 5 FP32 vectors for SIPG_PC_CHEB_F32) is allocated by the
+ * library and cached on the mesh. */
+int sipg_cg_solve(sipg_mesh* mesh, const sipg_cg_opts* opts, const double* b, double* x, int ncomp,
+                  void* stream, int* iters_out, double* relres_out);
+
+/* Adjoint gradient for a per-cell viscosity (not in the paper; the operator is
+ * the one of Sec. 3.2 (iii) in Laplace form): grad[e] = - lambda^T (dA/dnu_e) u
+ * for A(nu) = mass_coef M + L(nu), with lambda the solution of the adjoint
+ * system A lambda = dJ/du.  nu_cell, u, lambda: DEVICE (ncell, n_dofs, n_dofs
+ * doubles, one component); grad: DEVICE, ncell doubles.  On a face where the
+ * two viscosities are equal the penalty derivative is split half and half. */
+int sipg_adjoint_grad_nu(const sipg_mesh* mesh, const double* nu_cell, const double* u, const double* lambda,
+                         double* grad, void* stream);
+
+/* Choose the cells-per-block of the operator kernels for this mesh and
+ * precision (0 = FP64, 1 = FP32) by timing the candidates with CUDA events.
+ * If cache_path is not NULL the choice is read from / appended to that text
+ * file (one "key value" line per (k, precision, map, mesh size)). */
+int sipg_autotune(sipg_mesh* mesh, int precision, const char* cache_path);
+
+/* Cells per block currently used for a precision (host output). */
+int sipg_get_cells_per_block(const sipg_mesh* mesh, int precision, int* cpb);
+int sipg_set_cells_per_block(sipg_mesh* mesh, int precision, int cpb);
+
+/* Timing of the operator kernels: when enabled, CUDA events bracket every
+ * operator-apply launch issued by the library on the caller's stream, and
+ * sipg_profile_read returns the summed event time (ms), the number of timed
+ * applies and the number of kernels the library launched since the last reset
+ * (all kernels, timed or not).  Enabling adds an event record around each
+ * apply; it is off by default.  Graph replays are not bracketed. */
+int sipg_profile_enable(sipg_mesh* mesh, int on);
+int sipg_profile_read(sipg_mesh* mesh, int reset, double* apply_ms, long long* applies, long long* launches);
+
+/* Thread-local message describing the last error ("" if none). */
+const char* sipg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIPG_H */

@@ -229,14 +229,17 @@ class SIPG:
             return nu_cell
         return np.full(self.spec.ncell, float(nu))
 
-    def blocks(self, mass_coef=0.0, nu=1.0, nu_cell=None, stiffness=True):
+    def blocks(self, mass_coef=0.0, nu=1.0, nu_cell=None, stiffness=True, targets=None):
         """Yield (tgt_cells, src_cells, B) with B (n, P, P): y[tgt] += B @ x[src].
 
         This is the operator as a list of element-coupling blocks; ``apply`` and
-        ``assemble`` both consume it."""
+        ``assemble`` both consume it.  ``targets`` (bool mask over cells) keeps
+        only the blocks whose rows belong to those cells."""
         nue = self._nu(nu, nu_cell)
+        keep = (lambda c: targets[c]) if targets is not None else (lambda c: np.ones(len(c), dtype=bool))
         for kc in range(len(self.geom)):
             cells = np.nonzero(self.cell_key == kc)[0]
+            cells = cells[keep(cells)]
             if len(cells) == 0:
                 continue
             g = self.geom[kc]
@@ -250,12 +253,16 @@ class SIPG:
             nuF = np.maximum(nue[em], nue[ep])
             side_cells = (em, ep)
             for t in (MINUS, PLUS):
+                sel = keep(side_cells[t])
+                if not sel.any():
+                    continue
                 for s in (MINUS, PLUS):
-                    tgt, src = side_cells[t], side_cells[s]
+                    tgt, src = side_cells[t][sel], side_cells[s][sel]
                     B = (nue[src, None, None] * cu[t][s][None] + nue[tgt, None, None] * cv[t][s][None]
-                         + (tauF * nuF)[:, None, None] * pen[t][s][None])
+                         + (tauF[sel] * nuF[sel])[:, None, None] * pen[t][s][None])
                     yield tgt, src, B
         for d, side, bcells in self.bfaces:
+            bcells = bcells[keep(bcells)]
             for kc in np.unique(self.cell_key[bcells]):
                 cells = bcells[self.cell_key[bcells] == kc]
                 bcons, bpen = self.boundary_pieces(kc, d, side)
@@ -272,12 +279,7 @@ class SIPG:
         flat = x.ndim == 1
         X = x.reshape(-1, self.spec.ncell, self.P)
         Y = np.zeros_like(X)
-        for tgt, src, B in self.blocks(mass_coef, nu, nu_cell, stiffness):
-            if targets is not None:
-                sel = targets[tgt]
-                if not sel.any():
-                    continue
-                tgt, src, B = tgt[sel], src[sel], B[sel]
+        for tgt, src, B in self.blocks(mass_coef, nu, nu_cell, stiffness, targets):
             Y[:, tgt] += np.einsum("nij,cnj->cni", B, X[:, src])
         return Y.reshape(x.shape) if not flat else Y.ravel()
 
@@ -303,6 +305,13 @@ class SIPG:
             if self_mask.any():
                 D[tgt[self_mask]] += np.einsum("nii->ni", B[self_mask])
         return D.ravel()
+
+    def norm_inf(self, mass_coef=0.0, nu=1.0, nu_cell=None, stiffness=True, targets=None):
+        """max_i sum_j |A_ij| (over the rows of ``targets`` when given)."""
+        rows = np.zeros((self.spec.ncell, self.P))
+        for tgt, src, B in self.blocks(mass_coef, nu, nu_cell, stiffness, targets):
+            rows[tgt] += np.abs(B).sum(axis=2)
+        return float(rows.max())
 
     def mass_apply(self, x):
         return self.apply(x, mass_coef=1.0, stiffness=False)

@@ -1,5 +1,267 @@
 """GB300-native matrix-free SIPG operators (arXiv:1607.01323): Python binding.
 
-The binding is loaded lazily so that ``paper_1607_01323_gb300.inputs`` can be
-imported on a machine without the built library.
+A thin layer over the C ABI of ``include/sipg.h`` (libsipg.so).  It only
+marshals arguments: tensors become raw device pointers, the current torch
+stream becomes the CUDA stream.  Every computation runs in the library's
+kernels; there is no CPU fallback, and a missing library raises.
+
+The functions keep the C names without the ``sipg_`` prefix
+(``apply_laplace_f64``, ``cg_solve``, ...); ``Mesh`` wraps ``sipg_mesh``.
+The library is loaded lazily, so ``paper_1607_01323_gb300.inputs`` imports
+without it.
 """
+import ctypes as C
+
+from . import _lib as L
+
+__all__ = ["Mesh", "create_mesh", "apply_laplace_f64", "apply_laplace_f32", "apply_helmholtz_f64",
+           "apply_helmholtz_f32", "apply_mass_f64", "apply_inverse_mass_f64", "diagonal_f64", "cg_solve",
+           "adjoint_grad_nu", "autotune", "CgResult", "SipgError"]
+
+SipgError = L.SipgError
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s" % (name, dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return C.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A structured hexahedral mesh with its geometry tables on the current GPU.
+
+    n: cells per direction; lo, hi: box; bc_lo / bc_hi: 'periodic',
+    'dirichlet' or 'neumann' per direction; mapping: 'affine' or 'channel'
+    (tanh grading of y with parameter gamma); k: polynomial degree;
+    penalty: factor on tau of Eq. (taue)."""
+
+    def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc_lo=("periodic",) * 3,
+                 bc_hi=("periodic",) * 3, mapping="affine", gamma=1.8, k=3, penalty=1.0):
+        lib = L.lib()
+        d = L.MeshDesc()
+        for i in range(3):
+            d.n[i] = int(n[i])
+            d.lo[i] = float(lo[i])
+            d.hi[i] = float(hi[i])
+            d.bc_lo[i] = L.BC[bc_lo[i]]
+            d.bc_hi[i] = L.BC[bc_hi[i]]
+        d.map = L.MAP[mapping]
+        d.gamma = float(gamma)
+        h = C.c_void_p()
+        L.check(lib.sipg_create_mesh(C.byref(d), C.byref(h)))
+        self._h = h
+        self.n = tuple(int(v) for v in n)
+        self.bc_lo, self.bc_hi = tuple(bc_lo), tuple(bc_hi)
+        self.mapping, self.gamma = mapping, gamma
+        self.set_degree(k)
+        self.set_penalty(penalty)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and L._lib is not None:
+            L._lib.sipg_destroy_mesh(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_degree(self, k):
+        L.check(L.lib().sipg_set_degree(self._h, int(k)))
+        self.k = int(k)
+        self.p = self.k + 1
+
+    def set_penalty(self, factor):
+        L.check(L.lib().sipg_set_penalty(self._h, float(factor)))
+        self.penalty = float(factor)
+
+    @property
+    def n_dofs(self):
+        v = C.c_longlong()
+        L.check(L.lib().sipg_n_dofs(self._h, C.byref(v)))
+        return v.value
+
+    @property
+    def ncell(self):
+        v = C.c_longlong()
+        L.check(L.lib().sipg_n_cells(self._h, C.byref(v)))
+        return v.value
+
+    def node_coordinates(self):
+        """(n_dofs, 3) float64 numpy array of nodal point coordinates."""
+        import numpy as np
+        out = np.empty((self.n_dofs, 3), dtype=np.float64)
+        L.check(L.lib().sipg_node_coordinates(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def penalty_values(self):
+        import numpy as np
+        out = np.empty(self.ncell, dtype=np.float64)
+        L.check(L.lib().sipg_penalty_values(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def cells_per_block(self, precision=0):
+        v = C.c_int()
+        L.check(L.lib().sipg_get_cells_per_block(self._h, int(precision), C.byref(v)))
+        return v.value
+
+    def set_cells_per_block(self, precision, cpb):
+        L.check(L.lib().sipg_set_cells_per_block(self._h, int(precision), int(cpb)))
+
+    def profile_enable(self, on=True):
+        L.check(L.lib().sipg_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        """(summed apply ms, timed applies, kernels launched) since the last reset."""
+        ms, n, launches = C.c_double(), C.c_longlong(), C.c_longlong()
+        L.check(L.lib().sipg_profile_read(self._h, 1 if reset else 0, C.byref(ms), C.byref(n), C.byref(launches)))
+        return ms.value, n.value, launches.value
+
+
+def create_mesh(*args, **kw):
+    return Mesh(*args, **kw)
+
+
+def _ncomp(mesh, x):
+    n = mesh.n_dofs
+    if x.numel() % n != 0 or x.numel() == 0:
+        raise ValueError("vector length %d is not a multiple of n_dofs %d" % (x.numel(), n))
+    return x.numel() // n
+
+
+def _out(x, y):
+    torch = _torch()
+    return torch.empty_like(x) if y is None else y
+
+
+def apply_laplace_f64(mesh, x, y=None, stream=None):
+    torch = _torch()
+    y = _out(x, y)
+    L.check(L.lib().sipg_apply_laplace_f64(mesh.handle, _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y"),
+                                           _ncomp(mesh, x), _stream_ptr(stream)))
+    return y
+
+
+def apply_laplace_f32(mesh, x, y=None, stream=None):
+    torch = _torch()
+    y = _out(x, y)
+    L.check(L.lib().sipg_apply_laplace_f32(mesh.handle, _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
+                                           _ncomp(mesh, x), _stream_ptr(stream)))
+    return y
+
+
+def apply_helmholtz_f64(mesh, x, mass_coef, nu, nu_cell=None, y=None, stream=None):
+    torch = _torch()
+    y = _out(x, y)
+    nuc = _dev(nu_cell, torch.float64, "nu_cell") if nu_cell is not None else None
+    L.check(L.lib().sipg_apply_helmholtz_f64(mesh.handle, float(mass_coef), float(nu), nuc,
+                                             _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y"),
+                                             _ncomp(mesh, x), _stream_ptr(stream)))
+    return y
+
+
+def apply_helmholtz_f32(mesh, x, mass_coef, nu, nu_cell=None, y=None, stream=None):
+    torch = _torch()
+    y = _out(x, y)
+    nuc = _dev(nu_cell, torch.float32, "nu_cell") if nu_cell is not None else None
+    L.check(L.lib().sipg_apply_helmholtz_f32(mesh.handle, float(mass_coef), float(nu), nuc,
+                                             _dev(x, torch.float32, "x"), _dev(y, torch.float32, "y"),
+                                             _ncomp(mesh, x), _stream_ptr(stream)))
+    return y
+
+
+def apply_mass_f64(mesh, x, y=None, stream=None):
+    torch = _torch()
+    y = _out(x, y)
+    L.check(L.lib().sipg_apply_mass_f64(mesh.handle, _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y"),
+                                        _ncomp(mesh, x), _stream_ptr(stream)))
+    return y
+
+
+def apply_inverse_mass_f64(mesh, x, y=None, stream=None):
+    torch = _torch()
+    y = _out(x, y)
+    L.check(L.lib().sipg_apply_inverse_mass_f64(mesh.handle, _dev(x, torch.float64, "x"),
+                                                _dev(y, torch.float64, "y"), _ncomp(mesh, x), _stream_ptr(stream)))
+    return y
+
+
+def diagonal_f64(mesh, op="laplace", mass_coef=0.0, nu=1.0, nu_cell=None, out=None, stream=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty(mesh.n_dofs, dtype=torch.float64, device="cuda")
+    nuc = _dev(nu_cell, torch.float64, "nu_cell") if nu_cell is not None else None
+    L.check(L.lib().sipg_diagonal_f64(mesh.handle, L.OP[op], float(mass_coef), float(nu), nuc,
+                                      _dev(out, torch.float64, "diag"), _stream_ptr(stream)))
+    return out
+
+
+class CgResult:
+    def __init__(self, status, iters, relres):
+        self.status, self.iters, self.relres = status, iters, relres
+        self.converged = status == L.OK
+
+    def __repr__(self):
+        return "CgResult(status=%d, iters=%d, relres=%.3e)" % (self.status, self.iters, self.relres)
+
+
+def cg_opts(**kw):
+    o = L.CgOpts()
+    L.check(L.lib().sipg_cg_default_opts(C.byref(o)))
+    for key, v in kw.items():
+        if key == "op":
+            v = L.OP[v] if isinstance(v, str) else v
+        elif key == "precond":
+            v = L.PC[v] if isinstance(v, str) else v
+        elif key == "nu_cell":
+            v = v.data_ptr() if v is not None else None
+        setattr(o, key, v)
+    return o
+
+
+def cg_solve(mesh, b, x=None, stream=None, raise_on_fail=True, **opts):
+    """Solve A x = b (x holds the initial guess; zeros when None).  Keyword
+    options are the fields of sipg_cg_opts (op, precond, rtol, maxit, ...)."""
+    torch = _torch()
+    if x is None:
+        x = torch.zeros_like(b)
+    if opts.get("nu_cell") is not None:
+        _dev(opts["nu_cell"], torch.float64, "nu_cell")
+    o = cg_opts(**opts)
+    it, rel = C.c_int(), C.c_double()
+    st = L.lib().sipg_cg_solve(mesh.handle, C.byref(o), _dev(b, torch.float64, "b"), _dev(x, torch.float64, "x"),
+                               _ncomp(mesh, b), _stream_ptr(stream), C.byref(it), C.byref(rel))
+    if raise_on_fail:
+        L.check(st)
+    return x, CgResult(st, it.value, rel.value)
+
+
+def adjoint_grad_nu(mesh, nu_cell, u, lam, out=None, stream=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty(mesh.ncell, dtype=torch.float64, device="cuda")
+    L.check(L.lib().sipg_adjoint_grad_nu(mesh.handle, _dev(nu_cell, torch.float64, "nu_cell"),
+                                         _dev(u, torch.float64, "u"), _dev(lam, torch.float64, "lambda"),
+                                         _dev(out, torch.float64, "grad"), _stream_ptr(stream)))
+    return out
+
+
+def autotune(mesh, precision=0, cache_path=None):
+    L.check(L.lib().sipg_autotune(mesh.handle, int(precision), cache_path.encode() if cache_path else None))
+    return mesh.cells_per_block(precision)

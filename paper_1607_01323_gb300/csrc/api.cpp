@@ -1,0 +1,533 @@
+// C ABI of libsipg: argument validation, mesh lifetime, profiling and the
+// cells-per-block autotuner.  Every entry point returns a status and never
+// aborts; CUDA errors become SIPG_ECUDA with the runtime's message.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+
+#include "sipg_internal.h"
+
+namespace sipg {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int fail(int status, const std::string& msg) {
+  g_err = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return SIPG_ECUDA;
+}
+
+Mesh::~Mesh() {
+  for (int d = 0; d < 3; ++d) {
+    if (dtab64[d]) cudaFree(dtab64[d]);
+    if (dtab32[d]) cudaFree(dtab32[d]);
+  }
+  if (ws) cudaFree(ws);
+  for (auto& pr : pending) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+}
+
+template <typename T>
+Geo<T> make_geo(const Mesh& m) {
+  Geo<T> g;
+  for (int d = 0; d < 3; ++d) {
+    g.n[d] = m.desc.n[d];
+    g.bc_lo[d] = m.desc.bc_lo[d];
+    g.bc_hi[d] = m.desc.bc_hi[d];
+  }
+  g.ncell = (int)m.ncell;
+  for (int d = 0; d < 3; ++d) {
+    if (sizeof(T) == 8)
+      g.tab[d] = reinterpret_cast<const T*>(m.dtab64[d]);
+    else
+      g.tab[d] = reinterpret_cast<const T*>(m.dtab32[d]);
+  }
+  g.tau_scale = (T)(m.penalty * (m.k + 1) * (m.k + 1));
+  return g;
+}
+template Geo<double> make_geo<double>(const Mesh&);
+template Geo<float> make_geo<float>(const Mesh&);
+
+int default_cpb(int p, int precision) {
+  (void)precision;
+  switch (p) {
+    case 2: return 32;
+    case 3: return 16;
+    case 4: return 8;
+    case 5: return 8;
+    case 6: return 4;
+    case 7: return 4;
+    default: return 2;
+  }
+}
+
+void prof_begin(Mesh& m, cudaStream_t s, cudaEvent_t* e0) {
+  *e0 = nullptr;
+  if (!m.profile) return;
+  cudaEventCreate(e0);
+  cudaEventRecord(*e0, s);
+}
+
+void prof_end(Mesh& m, cudaStream_t s, cudaEvent_t e0) {
+  if (!m.profile || !e0) return;
+  cudaEvent_t e1;
+  cudaEventCreate(&e1);
+  cudaEventRecord(e1, s);
+  m.pending.emplace_back(e0, e1);
+}
+
+}  // namespace sipg
+
+using namespace sipg;
+
+struct sipg_mesh : public Mesh {};
+
+namespace {
+
+bool valid_bc(int b) { return b == SIPG_BC_PERIODIC || b == SIPG_BC_DIRICHLET || b == SIPG_BC_NEUMANN; }
+
+int check_mesh(const sipg_mesh* m) {
+  if (!m) return fail(SIPG_EINVAL, "mesh is NULL");
+  return SIPG_OK;
+}
+
+int check_vec(const void* x, const void* y, int ncomp) {
+  if (!x || !y) return fail(SIPG_EINVAL, "vector pointer is NULL");
+  if (ncomp < 1) return fail(SIPG_EINVAL, "ncomp must be >= 1");
+  if (x == y) return fail(SIPG_EINVAL, "x and y must not alias");
+  return SIPG_OK;
+}
+
+int set_device(const Mesh& m) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != m.device) {
+    e = cudaSetDevice(m.device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  }
+  return SIPG_OK;
+}
+
+long long n_dofs(const Mesh& m) { return m.ncell * m.p * m.p * m.p; }
+
+template <typename T>
+int apply_common(const sipg_mesh* mc, T cm, T nu, const T* nu_cell, bool stiffness, const T* x, T* y, int ncomp,
+                 void* stream) {
+  int st;
+  if ((st = check_mesh(mc))) return st;
+  if ((st = check_vec(x, y, ncomp))) return st;
+  if (!(cm >= T(0)) || !std::isfinite((double)cm)) return fail(SIPG_EINVAL, "mass_coef must be finite and >= 0");
+  if (stiffness && !nu_cell && !(nu > T(0))) return fail(SIPG_EINVAL, "nu must be > 0");
+  Mesh& m = const_cast<sipg_mesh&>(*mc);
+  if ((st = set_device(m))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0;
+  prof_begin(m, s, &e0);
+  st = launch_apply<T>(m, x, y, ncomp, cm, nu, nu_cell, stiffness, nullptr, nullptr, s);
+  prof_end(m, s, e0);
+  if (st == SIPG_OK && m.profile) m.prof_applies++;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sipg_last_error(void) { return g_err.c_str(); }
+
+int sipg_create_mesh(const sipg_mesh_desc* d, sipg_mesh** out) {
+  if (!d || !out) return fail(SIPG_EINVAL, "NULL argument");
+  *out = nullptr;
+  for (int i = 0; i < 3; ++i) {
+    if (d->n[i] < 1) return fail(SIPG_EINVAL, "cells per direction must be >= 1");
+    if (!(d->hi[i] > d->lo[i]) || !std::isfinite(d->lo[i]) || !std::isfinite(d->hi[i]))
+      return fail(SIPG_EINVAL, "box needs finite lo < hi");
+    if (!valid_bc(d->bc_lo[i]) || !valid_bc(d->bc_hi[i])) return fail(SIPG_EINVAL, "unknown boundary condition");
+    if ((d->bc_lo[i] == SIPG_BC_PERIODIC) != (d->bc_hi[i] == SIPG_BC_PERIODIC))
+      return fail(SIPG_EINVAL, "periodic sides must be paired");
+  }
+  if (d->map != SIPG_MAP_AFFINE && d->map != SIPG_MAP_CHANNEL_TANH) return fail(SIPG_EINVAL, "unknown map");
+  if (d->map == SIPG_MAP_CHANNEL_TANH && !(d->gamma > 0.0 && std::isfinite(d->gamma)))
+    return fail(SIPG_EINVAL, "channel map needs gamma > 0");
+  long long nc = (long long)d->n[0] * d->n[1] * d->n[2];
+  if (nc * 512 >= (1LL << 31) * 8LL) return fail(SIPG_EINVAL, "mesh too large");
+  if (nc >= (1LL << 31)) return fail(SIPG_EINVAL, "too many cells");
+  sipg_mesh* m = new (std::nothrow) sipg_mesh();
+  if (!m) return fail(SIPG_ENOMEM, "host allocation failed");
+  m->desc = *d;
+  m->ncell = nc;
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  m->k = 3;
+  m->p = 4;
+  int st = build_tables(*m);
+  if (st) {
+    delete m;
+    return st;
+  }
+  *out = m;
+  return SIPG_OK;
+}
+
+int sipg_destroy_mesh(sipg_mesh* m) {
+  if (!m) return SIPG_OK;
+  set_device(*m);
+  cudaDeviceSynchronize();
+  delete m;
+  return SIPG_OK;
+}
+
+int sipg_set_degree(sipg_mesh* m, int k) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (k < 1 || k > 7) return fail(SIPG_EINVAL, "degree must be 1 <= k <= 7");
+  if ((st = set_device(*m))) return st;
+  cudaDeviceSynchronize();
+  const int k0 = m->k;
+  m->k = k;
+  m->p = k + 1;
+  st = build_tables(*m);
+  if (st) {
+    m->k = k0;
+    m->p = k0 + 1;
+    build_tables(*m);
+    return st;
+  }
+  m->cpb[0] = m->cpb[1] = 0;
+  return SIPG_OK;
+}
+
+int sipg_set_penalty(sipg_mesh* m, double f) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!(f > 0.0) || !std::isfinite(f)) return fail(SIPG_EINVAL, "penalty factor must be > 0");
+  m->penalty = f;
+  return SIPG_OK;
+}
+
+int sipg_n_dofs(const sipg_mesh* m, long long* n) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!n) return fail(SIPG_EINVAL, "NULL output");
+  *n = n_dofs(*m);
+  return SIPG_OK;
+}
+
+int sipg_n_cells(const sipg_mesh* m, long long* n) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!n) return fail(SIPG_EINVAL, "NULL output");
+  *n = m->ncell;
+  return SIPG_OK;
+}
+
+int sipg_node_coordinates(const sipg_mesh* m, double* xyz) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!xyz) return fail(SIPG_EINVAL, "NULL output");
+  const int p = m->p;
+  std::vector<double> zn, wn;
+  gll_rule(p, zn, wn);
+  std::vector<double> X[3];
+  for (int d = 0; d < 3; ++d) {
+    const int n = m->desc.n[d];
+    X[d].resize((size_t)n * p);
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < p; ++a) X[d][(size_t)i * p + a] = map_coord(m->desc, d, (i + zn[a]) / n);
+  }
+  const int nx = m->desc.n[0], ny = m->desc.n[1];
+  long long idx = 0;
+  for (long long e = 0; e < m->ncell; ++e) {
+    const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)(e / ((long long)nx * ny));
+    for (int c = 0; c < p; ++c)
+      for (int b = 0; b < p; ++b)
+        for (int a = 0; a < p; ++a, ++idx) {
+          xyz[3 * idx + 0] = X[0][(size_t)ix * p + a];
+          xyz[3 * idx + 1] = X[1][(size_t)iy * p + b];
+          xyz[3 * idx + 2] = X[2][(size_t)iz * p + c];
+        }
+  }
+  return SIPG_OK;
+}
+
+int sipg_penalty_values(const sipg_mesh* m, double* tau) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!tau) return fail(SIPG_EINVAL, "NULL output");
+  const int p = m->p, nx = m->desc.n[0], ny = m->desc.n[1];
+  const double s = m->penalty * (m->k + 1) * (m->k + 1);
+  const int st_ = lstride(p);
+  for (long long e = 0; e < m->ncell; ++e) {
+    const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)(e / ((long long)nx * ny));
+    tau[e] = s * (m->htab[0][(size_t)ix * st_ + lay_t(p)] + m->htab[1][(size_t)iy * st_ + lay_t(p)] +
+                  m->htab[2][(size_t)iz * st_ + lay_t(p)]);
+  }
+  return SIPG_OK;
+}
+
+int sipg_apply_laplace_f64(const sipg_mesh* m, const double* x, double* y, int ncomp, void* stream) {
+  return apply_common<double>(m, 0.0, 1.0, nullptr, true, x, y, ncomp, stream);
+}
+
+int sipg_apply_laplace_f32(const sipg_mesh* m, const float* x, float* y, int ncomp, void* stream) {
+  return apply_common<float>(m, 0.f, 1.f, nullptr, true, x, y, ncomp, stream);
+}
+
+int sipg_apply_helmholtz_f64(const sipg_mesh* m, double cm, double nu, const double* nu_cell, const double* x,
+                             double* y, int ncomp, void* stream) {
+  return apply_common<double>(m, cm, nu, nu_cell, true, x, y, ncomp, stream);
+}
+
+int sipg_apply_helmholtz_f32(const sipg_mesh* m, float cm, float nu, const float* nu_cell, const float* x, float* y,
+                             int ncomp, void* stream) {
+  return apply_common<float>(m, cm, nu, nu_cell, true, x, y, ncomp, stream);
+}
+
+int sipg_apply_mass_f64(const sipg_mesh* m, const double* x, double* y, int ncomp, void* stream) {
+  return apply_common<double>(m, 1.0, 0.0, nullptr, false, x, y, ncomp, stream);
+}
+
+int sipg_apply_inverse_mass_f64(const sipg_mesh* mc, const double* x, double* y, int ncomp, void* stream) {
+  int st;
+  if ((st = check_mesh(mc))) return st;
+  if ((st = check_vec(x, y, ncomp))) return st;
+  Mesh& m = const_cast<sipg_mesh&>(*mc);
+  if ((st = set_device(m))) return st;
+  return launch_inverse_mass(m, x, y, ncomp, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int sipg_diagonal_f64(const sipg_mesh* mc, int op, double cm, double nu, const double* nu_cell, double* diag,
+                      void* stream) {
+  int st;
+  if ((st = check_mesh(mc))) return st;
+  if (!diag) return fail(SIPG_EINVAL, "diag is NULL");
+  if (op != SIPG_OP_LAPLACE && op != SIPG_OP_HELMHOLTZ) return fail(SIPG_EINVAL, "unknown operator");
+  Mesh& m = const_cast<sipg_mesh&>(*mc);
+  if ((st = set_device(m))) return st;
+  if (op == SIPG_OP_LAPLACE) return launch_diagonal(m, true, 0.0, 1.0, nullptr, diag, (cudaStream_t)stream);
+  if (!(cm >= 0.0) || (!nu_cell && !(nu > 0.0))) return fail(SIPG_EINVAL, "need mass_coef >= 0 and nu > 0");
+  return launch_diagonal(m, true, cm, nu, nu_cell, diag, (cudaStream_t)stream);
+}
+
+int sipg_cg_default_opts(sipg_cg_opts* o) {
+  if (!o) return fail(SIPG_EINVAL, "NULL opts");
+  std::memset(o, 0, sizeof(*o));
+  o->op = SIPG_OP_LAPLACE;
+  o->mass_coef = 0.0;
+  o->nu = 1.0;
+  o->nu_cell = nullptr;
+  o->precond = SIPG_PC_JACOBI;
+  o->cheb_degree = 4;
+  o->cheb_range = 20.0;
+  o->cheb_lmax = 0.0;
+  o->cheb_lanczos_steps = 20;
+  o->zero_mean = 0;
+  o->rtol = 1e-10;
+  o->maxit = 10000;
+  o->flexible = 0;
+  o->use_graph = 1;
+  o->check_every = 16;
+  return SIPG_OK;
+}
+
+int sipg_cg_solve(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* x, int ncomp, void* stream,
+                  int* iters, double* relres) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!o) return fail(SIPG_EINVAL, "opts is NULL");
+  if ((st = check_vec(b, x, ncomp))) return st;
+  if (o->op != SIPG_OP_LAPLACE && o->op != SIPG_OP_HELMHOLTZ) return fail(SIPG_EINVAL, "unknown operator");
+  if (o->op == SIPG_OP_HELMHOLTZ && (!(o->mass_coef >= 0.0) || (!o->nu_cell && !(o->nu > 0.0))))
+    return fail(SIPG_EINVAL, "Helmholtz needs mass_coef >= 0 and nu > 0");
+  if (o->precond < SIPG_PC_NONE || o->precond > SIPG_PC_CHEB_F32) return fail(SIPG_EINVAL, "unknown preconditioner");
+  if (o->precond == SIPG_PC_CHEB_F32) {
+    if (o->cheb_degree < 1 || o->cheb_degree > 64) return fail(SIPG_EINVAL, "cheb_degree must be in [1, 64]");
+    if (!(o->cheb_range > 1.0)) return fail(SIPG_EINVAL, "cheb_range must be > 1");
+    if (!(o->cheb_lmax > 0.0) && (o->cheb_lanczos_steps < 2 || o->cheb_lanczos_steps > 128))
+      return fail(SIPG_EINVAL, "cheb_lanczos_steps must be in [2, 128]");
+    if (o->op == SIPG_OP_HELMHOLTZ && o->nu_cell)
+      return fail(SIPG_EINVAL, "the FP32 Chebyshev preconditioner supports a constant nu only");
+  }
+  if (!(o->rtol >= 0.0) || o->maxit < 1) return fail(SIPG_EINVAL, "need rtol >= 0 and maxit >= 1");
+  if (o->check_every < 1 || o->check_every > 4096) return fail(SIPG_EINVAL, "check_every must be in [1, 4096]");
+  bool all_bc_free = true;  // singular operator: all sides periodic or Neumann, Laplace
+  for (int d = 0; d < 3; ++d)
+    if (m->desc.bc_lo[d] == SIPG_BC_DIRICHLET || m->desc.bc_hi[d] == SIPG_BC_DIRICHLET) all_bc_free = false;
+  if (all_bc_free && o->op == SIPG_OP_LAPLACE && !o->zero_mean)
+    return fail(SIPG_EINVAL, "singular Laplace problem (no Dirichlet side): set zero_mean");
+  if ((st = set_device(*m))) return st;
+  // The solve runs on a private non-blocking stream joined to the caller's
+  // stream with events, so that graph capture also works when the caller uses
+  // the legacy default stream.
+  cudaStream_t cs = (cudaStream_t)stream, s = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(s);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  cudaEventRecord(ev, cs);
+  cudaStreamWaitEvent(s, ev, 0);
+  st = cg_solve(*m, *o, b, x, ncomp, s, iters, relres);
+  cudaEventRecord(ev, s);
+  cudaStreamWaitEvent(cs, ev, 0);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(s);
+  return st;
+}
+
+int sipg_adjoint_grad_nu(const sipg_mesh* mc, const double* nu_cell, const double* u, const double* lam,
+                         double* grad, void* stream) {
+  int st;
+  if ((st = check_mesh(mc))) return st;
+  if (!nu_cell || !u || !lam || !grad) return fail(SIPG_EINVAL, "NULL argument");
+  Mesh& m = const_cast<sipg_mesh&>(*mc);
+  if ((st = set_device(m))) return st;
+  return launch_adjoint(m, nu_cell, u, lam, grad, (cudaStream_t)stream);
+}
+
+int sipg_get_cells_per_block(const sipg_mesh* m, int precision, int* cpb) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!cpb || (precision != 0 && precision != 1)) return fail(SIPG_EINVAL, "bad argument");
+  *cpb = m->cpb[precision] > 0 ? m->cpb[precision] : default_cpb(m->p, precision);
+  return SIPG_OK;
+}
+
+int sipg_set_cells_per_block(sipg_mesh* m, int precision, int cpb) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (precision != 0 && precision != 1) return fail(SIPG_EINVAL, "precision must be 0 or 1");
+  const size_t elt = precision == 0 ? 8 : 4;
+  if (cpb < 1 || (cpb * m->p * m->p + 31) / 32 * 32 > kMaxCellThreads || (size_t)3 * cpb * m->p * m->p * m->p * elt > 200 * 1024)
+    return fail(SIPG_EINVAL, "cells per block out of range for this degree");
+  m->cpb[precision] = cpb;
+  return SIPG_OK;
+}
+
+int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (precision != 0 && precision != 1) return fail(SIPG_EINVAL, "precision must be 0 or 1");
+  char key[160];
+  std::snprintf(key, sizeof(key), "k=%d prec=%d map=%d n=%dx%dx%d", m->k, precision, m->desc.map, m->desc.n[0],
+                m->desc.n[1], m->desc.n[2]);
+  if (cache_path) {
+    std::ifstream f(cache_path);
+    std::string line;
+    while (std::getline(f, line)) {
+      const size_t bar = line.rfind(" cpb=");
+      if (bar != std::string::npos && line.substr(0, bar) == key) {
+        const int c = std::atoi(line.c_str() + bar + 5);
+        if (sipg_set_cells_per_block(m, precision, c) == SIPG_OK) return SIPG_OK;
+      }
+    }
+  }
+  if ((st = set_device(*m))) return st;
+  const size_t elt = precision == 0 ? 8 : 4;
+  const long long n = n_dofs(*m);
+  void *x = nullptr, *y = nullptr;
+  cudaError_t e = cudaMalloc(&x, n * elt);
+  if (e == cudaSuccess) e = cudaMalloc(&y, n * elt);
+  if (e != cudaSuccess) {
+    if (x) cudaFree(x);
+    return fail(SIPG_ENOMEM, "autotune buffers");
+  }
+  cudaMemset(x, 0, n * elt);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = 0;
+  float best_ms = 1e30f;
+  const int old = m->cpb[precision];
+  for (int c = 1; c <= 64; c *= 2) {
+    if (sipg_set_cells_per_block(m, precision, c) != SIPG_OK) continue;
+    float tot = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep) {
+      cudaEventRecord(e0, 0);
+      for (int it = 0; it < 3; ++it) {
+        int s2 = precision == 0 ? launch_apply<double>(*m, (double*)x, (double*)y, 1, 0.0, 1.0, nullptr, true, nullptr,
+                                                       nullptr, 0)
+                                : launch_apply<float>(*m, (float*)x, (float*)y, 1, 0.f, 1.f, nullptr, true, nullptr,
+                                                      nullptr, 0);
+        if (s2) ok = false;
+      }
+      cudaEventRecord(e1, 0);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;  // first repetition is warm-up
+    }
+    if (ok && tot < best_ms) {
+      best_ms = tot;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  cudaGetLastError();
+  if (best == 0) {
+    m->cpb[precision] = old;
+    return fail(SIPG_ECUDA, "autotune: no candidate ran");
+  }
+  m->cpb[precision] = best;
+  if (cache_path) {
+    std::ofstream f(cache_path, std::ios::app);
+    if (f) f << key << " cpb=" << best << "\n";
+  }
+  return SIPG_OK;
+}
+
+int sipg_profile_enable(sipg_mesh* m, int on) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  m->profile = on != 0;
+  return SIPG_OK;
+}
+
+int sipg_profile_read(sipg_mesh* m, int reset, double* apply_ms, long long* applies, long long* launches) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  for (auto& pr : m->pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(pr.second);
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) m->prof_ms += ms;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  m->pending.clear();
+  cudaGetLastError();
+  if (apply_ms) *apply_ms = m->prof_ms;
+  if (applies) *applies = m->prof_applies;
+  if (launches) *launches = m->launches;
+  if (reset) {
+    m->prof_ms = 0.0;
+    m->prof_applies = 0;
+    m->launches = 0;
+  }
+  return SIPG_OK;
+}
+
+}  // extern "C"

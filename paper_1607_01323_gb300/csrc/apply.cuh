@@ -1,0 +1,503 @@
+// Matrix-free SIPG kernels for sm_103a (templated on the scalar type and on
+// p = k+1).
+//
+// Operator (Sec. 3.2 (ii)/(iii), Sec. 5).  For a separable iso-parametric map
+// the Jacobian is diagonal and depends on one reference coordinate per
+// direction, so every cell and face integral of the SIPG form factorises into
+// 1D matrices (M: mass, K: stiffness, per direction and layer).  Sum
+// factorisation then applies the operator of one cell e as
+//
+//   y_e = (I x My x Mz) w_x + (Mx x I x Mz) w_y + (Mx x My x I) w_z
+//
+// where w_d is a 1D operator along direction d acting on every line of the
+// cell: nu_e K_d u plus the two face terms of Sec. 3.2 (ii) in that direction
+// (jump and average with the neighbour's line, penalty tau_F nu_F with tau of
+// Eq. (taue)/(tau)), and for the Helmholtz operator w_z also carries the mass
+// term mass_coef Mz u.  The transverse mass matrices of a face are the cell's
+// own 1D mass matrices (the face quadrature is the cell quadrature restricted
+// to the face), which is why the face terms enter w_d before the transverse
+// contractions.  Evaluation order per cell (lines owned by one thread each):
+//   X: w_x (x-lines)              Y: w_y (y-lines)
+//   Z: w_z, A1 = Mz w_x, A2 = Mz w_y (z-lines)
+//   Y2: R1 = My A1, R2 = My w_z + A2 (y-lines)
+//   X2: y = Mx R2 + R1 (x-lines) -> global
+// 8 contractions of p FMAs per DoF plus the face terms.  Faces are handled
+// cell-centrically: every cell reads its six neighbours' lines and writes only
+// its own outputs, so there are no atomics and the result is deterministic.
+#pragma once
+
+#include "sipg_internal.h"
+
+namespace sipg {
+
+template <int P>
+struct LayerOff {
+  static constexpr int M = 0, K = P * P, Mi = 2 * P * P, dL = 3 * P * P, dR = 3 * P * P + P, h = 3 * P * P + 2 * P,
+                       t = 3 * P * P + 2 * P + 1, stride = 3 * P * P + 2 * P + 4;
+};
+
+// Neighbour across side (0 = low, 1 = high) of direction dir.  kind: 0 interior
+// (or periodic), SIPG_BC_DIRICHLET, SIPG_BC_NEUMANN.
+template <typename T>
+__device__ __forceinline__ void face_neighbor(const Geo<T>& g, int dir, int side, int id, int e, int& nb, int& kind,
+                                              int& jlayer) {
+  const int n = g.n[dir];
+  int j = id + (side ? 1 : -1);
+  const int bc = side ? g.bc_hi[dir] : g.bc_lo[dir];
+  kind = 0;
+  if (j < 0 || j >= n) {
+    if (bc == SIPG_BC_PERIODIC) {
+      j = (j + n) % n;
+    } else {
+      kind = bc;
+      nb = -1;
+      jlayer = -1;
+      return;
+    }
+  }
+  const int stride = dir == 0 ? 1 : (dir == 1 ? g.n[0] : g.n[0] * g.n[1]);
+  nb = e + (j - id) * stride;
+  jlayer = j;
+}
+
+// The 1D operator of one line along one direction: nu_e K u + face terms
+// (+ cm Mm u when mass is true).  uL / uR are the neighbours' lines at the same
+// transverse position, LL / LR their layer tables.
+template <typename T, int P>
+__device__ __forceinline__ void line_op(T (&w)[P], const T (&u)[P], const T* __restrict__ L, T nue, bool stiffness,
+                                        T cm, bool mass, int kindL, const T (&uL)[P], const T* __restrict__ LL,
+                                        T nuL, T tauFL, int kindR, const T (&uR)[P], const T* __restrict__ LR, T nuR,
+                                        T tauFR, T tau_e) {
+  using O = LayerOff<P>;
+#pragma unroll
+  for (int a = 0; a < P; ++a) w[a] = T(0);
+  if (stiffness) {
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < P; ++b) s = fma(L[O::K + a * P + b], u[b], s);
+      w[a] = nue * s;
+    }
+    // high face: this cell is the "-" side, n points out of it
+    if (kindR == 0) {
+      T gO = T(0), gN = T(0);
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        gO = fma(L[O::dR + a], u[a], gO);
+        gN = fma(LR[O::dL + a], uR[a], gN);
+      }
+      const T J = u[P - 1] - uR[0];
+      const T avg = T(0.5) * (nue * gO + nuR * gN);
+      const T tn = tauFR * (nue > nuR ? nue : nuR);
+      w[P - 1] += tn * J - avg;
+      const T c = T(-0.5) * nue * J;
+#pragma unroll
+      for (int a = 0; a < P; ++a) w[a] = fma(c, L[O::dR + a], w[a]);
+    } else if (kindR == SIPG_BC_DIRICHLET) {
+      T gO = T(0);
+#pragma unroll
+      for (int a = 0; a < P; ++a) gO = fma(L[O::dR + a], u[a], gO);
+      w[P - 1] += T(2) * tau_e * nue * u[P - 1] - nue * gO;
+      const T c = -nue * u[P - 1];
+#pragma unroll
+      for (int a = 0; a < P; ++a) w[a] = fma(c, L[O::dR + a], w[a]);
+    }
+    // low face: this cell is the "+" side, n points into it
+    if (kindL == 0) {
+      T gO = T(0), gN = T(0);
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        gO = fma(L[O::dL + a], u[a], gO);
+        gN = fma(LL[O::dR + a], uL[a], gN);
+      }
+      const T J = uL[P - 1] - u[0];
+      const T avg = T(0.5) * (nuL * gN + nue * gO);
+      const T tn = tauFL * (nue > nuL ? nue : nuL);
+      w[0] += avg - tn * J;
+      const T c = T(-0.5) * nue * J;
+#pragma unroll
+      for (int a = 0; a < P; ++a) w[a] = fma(c, L[O::dL + a], w[a]);
+    } else if (kindL == SIPG_BC_DIRICHLET) {
+      T gO = T(0);
+#pragma unroll
+      for (int a = 0; a < P; ++a) gO = fma(L[O::dL + a], u[a], gO);
+      w[0] += nue * gO + T(2) * tau_e * nue * u[0];
+      const T c = nue * u[0];
+#pragma unroll
+      for (int a = 0; a < P; ++a) w[a] = fma(c, L[O::dL + a], w[a]);
+    }
+  }
+  if (mass) {
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < P; ++b) s = fma(L[O::M + a * P + b], u[b], s);
+      w[a] = fma(cm, s, w[a]);
+    }
+  }
+}
+
+// y[a] = sum_b A[a][b] v[b] (+ y[a] when acc)
+template <typename T, int P>
+__device__ __forceinline__ void matvec(T (&out)[P], const T* __restrict__ A, const T (&v)[P]) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < P; ++b) s = fma(A[a * P + b], v[b], s);
+    out[a] = s;
+  }
+}
+
+// Index of element (a, b, c) inside one cell.
+template <int P>
+__device__ __forceinline__ int nidx(int a, int b, int c) {
+  return (c * P + b) * P + a;
+}
+
+// Stride between consecutive line entries and line start for direction dir and
+// transverse thread coordinates (ti, tj): x-line (b=ti, c=tj), y-line (a=ti,
+// c=tj), z-line (a=ti, b=tj).
+template <int P>
+__device__ __forceinline__ void line_geom(int dir, int ti, int tj, int& start, int& step) {
+  if (dir == 0) {
+    start = nidx<P>(0, ti, tj);
+    step = 1;
+  } else if (dir == 1) {
+    start = nidx<P>(ti, 0, tj);
+    step = P;
+  } else {
+    start = nidx<P>(ti, tj, 0);
+    step = P * P;
+  }
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void load_line(T (&v)[P], const T* __restrict__ base, int start, int step) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) v[a] = base[start + a * step];
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void load_line_global(T (&v)[P], const T* __restrict__ base, int start, int step) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) v[a] = __ldg(base + start + a * step);
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void store_line(T* base, const T (&v)[P], int start, int step) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) base[start + a * step] = v[a];
+}
+
+// Block reduction of three doubles; thread 0 writes out[0..2].
+__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out) {
+  __shared__ double red[3][32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+    red[2][wid] = c;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    a = lane < nw ? red[0][lane] : 0.0;
+    b = lane < nw ? red[1][lane] : 0.0;
+    c = lane < nw ? red[2][lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+      c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+      out[0] = a;
+      out[1] = b;
+      out[2] = c;
+    }
+  }
+}
+
+// Per-direction data of one line operator for cell e.
+template <typename T, int P>
+struct DirCtx {
+  const T* L;
+  const T* LL;
+  const T* LR;
+  int kindL, kindR, nbL, nbR;
+  T nuL, nuR, tauFL, tauFR;
+};
+
+template <typename T, int P>
+__device__ __forceinline__ DirCtx<T, P> dir_ctx(const Geo<T>& g, int dir, const int (&id)[3], int e, T nue, T tau_e,
+                                                const T* __restrict__ nu_cell, T nu) {
+  using O = LayerOff<P>;
+  DirCtx<T, P> c;
+  c.L = g.tab[dir] + id[dir] * O::stride;
+  const T t_own = c.L[O::t];
+  int jl, jr;
+  face_neighbor(g, dir, 0, id[dir], e, c.nbL, c.kindL, jl);
+  face_neighbor(g, dir, 1, id[dir], e, c.nbR, c.kindR, jr);
+  c.LL = c.L;
+  c.LR = c.L;
+  c.nuL = c.nuR = nue;
+  c.tauFL = c.tauFR = tau_e;
+  if (c.kindL == 0) {
+    c.LL = g.tab[dir] + jl * O::stride;
+    c.nuL = nu_cell ? __ldg(nu_cell + c.nbL) : nu;
+    const T tn = tau_e + g.tau_scale * (c.LL[O::t] - t_own);
+    c.tauFL = tn > tau_e ? tn : tau_e;
+  }
+  if (c.kindR == 0) {
+    c.LR = g.tab[dir] + jr * O::stride;
+    c.nuR = nu_cell ? __ldg(nu_cell + c.nbR) : nu;
+    const T tn = tau_e + g.tau_scale * (c.LR[O::t] - t_own);
+    c.tauFR = tn > tau_e ? tn : tau_e;
+  }
+  return c;
+}
+
+// y = mass_coef M x + nu L x for CPB cells per block, p^2 threads per cell.
+template <typename T, int P>
+__global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const T* __restrict__ x, T* __restrict__ y, int cpb,
+                                                     T mass_coef, T nu, const T* __restrict__ nu_cell, int stiffness,
+                                                     double* __restrict__ dots) {
+  constexpr int P2 = P * P, P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);
+  T* s1 = su + cpb * P3;
+  T* s2 = s1 + cpb * P3;
+  const int cs = threadIdx.x / P2;
+  const int t = threadIdx.x - cs * P2;
+  const int ti = t % P, tj = t / P;
+  const long long cell0 = (long long)blockIdx.x * cpb;
+  const int e = (int)(cell0 + cs);
+  const bool active = cs < cpb && e < g.ncell;  // blocks are rounded up to whole warps
+  const long long cbase = (long long)blockIdx.y * g.ncell * P3;
+  const T* __restrict__ xc = x + cbase;
+  {
+    const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
+    const T* xb = xc + cell0 * P3;
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = xb[idx];
+  }
+  __syncthreads();
+  T* us = su + cs * P3;
+  T* w1 = s1 + cs * P3;
+  T* w2 = s2 + cs * P3;
+  int id[3] = {0, 0, 0};
+  T nue = nu, tau_e = T(0);
+  const bool stiff = stiffness != 0;
+  if (active) {
+    id[0] = e % g.n[0];
+    id[1] = (e / g.n[0]) % g.n[1];
+    id[2] = e / (g.n[0] * g.n[1]);
+    if (nu_cell) nue = __ldg(nu_cell + e);
+    using O = LayerOff<P>;
+    tau_e = g.tau_scale * (g.tab[0][id[0] * O::stride + O::t] + g.tab[1][id[1] * O::stride + O::t] +
+                           g.tab[2][id[2] * O::stride + O::t]);
+  }
+  T ux[P];  // this thread's x-line of x, kept for the dot products
+  if (active) {
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      int start, step;
+      line_geom<P>(dir, ti, tj, start, step);
+      T u[P], uL[P], uR[P], w[P];
+      load_line<T, P>(u, us, start, step);
+      if (dir == 0) {
+#pragma unroll
+        for (int a = 0; a < P; ++a) ux[a] = u[a];
+      }
+      if (stiff) {
+        DirCtx<T, P> c = dir_ctx<T, P>(g, dir, id, e, nue, tau_e, nu_cell, nu);
+        if (c.kindL == 0) load_line_global<T, P>(uL, xc + (long long)c.nbL * P3, start, step);
+        if (c.kindR == 0) load_line_global<T, P>(uR, xc + (long long)c.nbR * P3, start, step);
+        line_op<T, P>(w, u, c.L, nue, true, T(0), false, c.kindL, uL, c.LL, c.nuL, c.tauFL, c.kindR, uR, c.LR, c.nuR,
+                      c.tauFR, tau_e);
+      } else {
+#pragma unroll
+        for (int a = 0; a < P; ++a) w[a] = T(0);
+      }
+      store_line<T, P>(dir == 0 ? w1 : w2, w, start, step);
+    }
+  }
+  __syncthreads();
+  if (active) {
+    int start, step;
+    line_geom<P>(2, ti, tj, start, step);
+    T u[P], uL[P], uR[P], w[P], v1[P], v2[P], a1[P], a2[P];
+    load_line<T, P>(u, us, start, step);
+    DirCtx<T, P> c = dir_ctx<T, P>(g, 2, id, e, nue, tau_e, nu_cell, nu);
+    if (stiff) {
+      if (c.kindL == 0) load_line_global<T, P>(uL, xc + (long long)c.nbL * P3, start, step);
+      if (c.kindR == 0) load_line_global<T, P>(uR, xc + (long long)c.nbR * P3, start, step);
+    }
+    line_op<T, P>(w, u, c.L, nue, stiff, mass_coef, mass_coef != T(0), c.kindL, uL, c.LL, c.nuL, c.tauFL, c.kindR, uR,
+                  c.LR, c.nuR, c.tauFR, tau_e);
+    load_line<T, P>(v1, w1, start, step);
+    load_line<T, P>(v2, w2, start, step);
+    matvec<T, P>(a1, c.L + LayerOff<P>::M, v1);
+    matvec<T, P>(a2, c.L + LayerOff<P>::M, v2);
+    store_line<T, P>(us, w, start, step);
+    store_line<T, P>(w1, a1, start, step);
+    store_line<T, P>(w2, a2, start, step);
+  }
+  __syncthreads();
+  if (active) {
+    int start, step;
+    line_geom<P>(1, ti, tj, start, step);
+    const T* My = g.tab[1] + id[1] * LayerOff<P>::stride + LayerOff<P>::M;
+    T v[P], r1[P], r2[P], a2[P];
+    load_line<T, P>(v, w1, start, step);
+    matvec<T, P>(r1, My, v);
+    load_line<T, P>(v, us, start, step);
+    matvec<T, P>(r2, My, v);
+    load_line<T, P>(a2, w2, start, step);
+#pragma unroll
+    for (int a = 0; a < P; ++a) r2[a] += a2[a];
+    store_line<T, P>(w1, r1, start, step);
+    store_line<T, P>(w2, r2, start, step);
+  }
+  __syncthreads();
+  double d_xy = 0.0, d_y = 0.0, d_x = 0.0;
+  if (active) {
+    int start, step;
+    line_geom<P>(0, ti, tj, start, step);
+    const T* Mx = g.tab[0] + id[0] * LayerOff<P>::stride + LayerOff<P>::M;
+    T v[P], out[P], r1[P];
+    load_line<T, P>(v, w2, start, step);
+    matvec<T, P>(out, Mx, v);
+    load_line<T, P>(r1, w1, start, step);
+    T* yo = y + cbase + (long long)e * P3 + start;
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      out[a] += r1[a];
+      yo[a] = out[a];
+    }
+    if (dots) {
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        d_xy += (double)out[a] * (double)ux[a];
+        d_y += (double)out[a];
+        d_x += (double)ux[a];
+      }
+    }
+  }
+  if (dots) block_reduce3(d_xy, d_y, d_x, dots + 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// y = M^-1 x = (Mx^-1 x My^-1 x Mz^-1) x cell by cell (Sec. 5: tensorial inverse
+// mass with square 1D transforms).  Optional dots as in apply_kernel (x.y).
+template <int P>
+__global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<double> g, const double* __restrict__ x,
+                                                            double* __restrict__ y, int cpb, double* __restrict__ dots) {
+  constexpr int P2 = P * P, P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* su = reinterpret_cast<double*>(smem_raw);
+  const int cs = threadIdx.x / P2;
+  const int t = threadIdx.x - cs * P2;
+  const int ti = t % P, tj = t / P;
+  const long long cell0 = (long long)blockIdx.x * cpb;
+  const int e = (int)(cell0 + cs);
+  const bool active = cs < cpb && e < g.ncell;  // blocks are rounded up to whole warps
+  const long long cbase = (long long)blockIdx.y * g.ncell * P3;
+  {
+    const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
+    const double* xb = x + cbase + cell0 * P3;
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = xb[idx];
+  }
+  __syncthreads();
+  double* us = su + cs * P3;
+  int id[3] = {0, 0, 0};
+  if (active) {
+    id[0] = e % g.n[0];
+    id[1] = (e / g.n[0]) % g.n[1];
+    id[2] = e / (g.n[0] * g.n[1]);
+  }
+  using O = LayerOff<P>;
+  for (int dir = 2; dir >= 1; --dir) {
+    if (active) {
+      int start, step;
+      line_geom<P>(dir, ti, tj, start, step);
+      double v[P], o[P];
+      load_line<double, P>(v, us, start, step);
+      matvec<double, P>(o, g.tab[dir] + id[dir] * O::stride + O::Mi, v);
+      store_line<double, P>(us, o, start, step);
+    }
+    __syncthreads();
+  }
+  double d_xy = 0.0, d_y = 0.0, d_x = 0.0;
+  if (active) {
+    int start, step;
+    line_geom<P>(0, ti, tj, start, step);
+    double v[P], o[P];
+    load_line<double, P>(v, us, start, step);
+    matvec<double, P>(o, g.tab[0] + id[0] * O::stride + O::Mi, v);
+    const long long off = cbase + (long long)e * P3 + start;
+    for (int a = 0; a < P; ++a) y[off + a] = o[a];
+    if (dots) {
+      for (int a = 0; a < P; ++a) {
+        const double xv = x[off + a];
+        d_xy += o[a] * xv;
+        d_y += o[a];
+        d_x += xv;
+      }
+    }
+  }
+  if (dots) block_reduce3(d_xy, d_y, d_x, dots + 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// diag(A) in closed form: the self-coupling of the 1D line operators on the
+// diagonal, times the diagonals of the transverse 1D mass matrices.
+template <int P>
+__global__ void diagonal_kernel(Geo<double> g, int stiffness, double mass_coef, double nu,
+                                const double* __restrict__ nu_cell, double* __restrict__ diag) {
+  constexpr int P3 = P * P * P;
+  using O = LayerOff<P>;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)g.ncell * P3) return;
+  const int e = (int)(i / P3);
+  const int r = (int)(i - (long long)e * P3);
+  const int idx[3] = {r % P, (r / P) % P, r / (P * P)};
+  int id[3];
+  id[0] = e % g.n[0];
+  id[1] = (e / g.n[0]) % g.n[1];
+  id[2] = e / (g.n[0] * g.n[1]);
+  const double nue = nu_cell ? nu_cell[e] : nu;
+  const double tau_e = g.tau_scale * (g.tab[0][id[0] * O::stride + O::t] + g.tab[1][id[1] * O::stride + O::t] +
+                                      g.tab[2][id[2] * O::stride + O::t]);
+  double md[3], kd[3];
+  for (int dir = 0; dir < 3; ++dir) {
+    DirCtx<double, P> c = dir_ctx<double, P>(g, dir, id, e, nue, tau_e, nu_cell, nu);
+    const int a = idx[dir];
+    md[dir] = c.L[O::M + a * P + a];
+    double k = nue * c.L[O::K + a * P + a];
+    if (a == P - 1) {
+      if (c.kindR == 0)
+        k += -nue * c.L[O::dR + P - 1] + c.tauFR * (nue > c.nuR ? nue : c.nuR);
+      else if (c.kindR == SIPG_BC_DIRICHLET)
+        k += -2.0 * nue * c.L[O::dR + P - 1] + 2.0 * tau_e * nue;
+    }
+    if (a == 0) {
+      if (c.kindL == 0)
+        k += nue * c.L[O::dL] + c.tauFL * (nue > c.nuL ? nue : c.nuL);
+      else if (c.kindL == SIPG_BC_DIRICHLET)
+        k += 2.0 * nue * c.L[O::dL] + 2.0 * tau_e * nue;
+    }
+    kd[dir] = k;
+  }
+  double v = mass_coef * md[0] * md[1] * md[2];
+  if (stiffness) v += kd[0] * md[1] * md[2] + md[0] * kd[1] * md[2] + md[0] * md[1] * kd[2];
+  diag[i] = v;
+}
+
+}  // namespace sipg

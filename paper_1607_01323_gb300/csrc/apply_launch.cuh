@@ -1,0 +1,45 @@
+// Launchers of the operator kernel for one scalar type (included by
+// apply_f64.cu and apply_f32.cu so that the two compile in parallel).
+#pragma once
+
+#include "apply.cuh"
+
+namespace sipg {
+
+template <typename T, int P>
+static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu, const T* nu_cell, bool stiff,
+                          double* dots, int* nblocks, cudaStream_t s) {
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  const int cpb = m.cpb[prec] > 0 ? m.cpb[prec] : default_cpb(P, prec);
+  const Geo<T> g = make_geo<T>(m);
+  const dim3 grid((unsigned)((m.ncell + cpb - 1) / cpb), (unsigned)ncomp);
+  const int threads = (cpb * P * P + 31) / 32 * 32;  // whole warps (the block reduction shuffles full warps)
+  const size_t smem = (size_t)3 * cpb * P * P * P * sizeof(T);
+  if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
+  }
+  apply_kernel<T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm, nu, nu_cell, stiff ? 1 : 0, dots);
+  if (nblocks) *nblocks = (int)(grid.x * grid.y);
+  const_cast<Mesh&>(m).launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch");
+}
+
+template <typename T>
+static int launch_apply_dispatch(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu, const T* nu_cell, bool stiff,
+                                 double* dots, int* nblocks, cudaStream_t s) {
+  switch (m.p) {
+    case 2: return launch_apply_p<T, 2>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+    case 3: return launch_apply_p<T, 3>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+    case 4: return launch_apply_p<T, 4>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+    case 5: return launch_apply_p<T, 5>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+    case 6: return launch_apply_p<T, 6>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+    case 7: return launch_apply_p<T, 7>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+    case 8: return launch_apply_p<T, 8>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+    default: return fail(SIPG_EINVAL, "unsupported degree");
+  }
+}
+
+}  // namespace sipg

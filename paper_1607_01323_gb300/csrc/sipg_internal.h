@@ -1,0 +1,121 @@
+// Internal declarations of libsipg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sipg.h"
+
+namespace sipg {
+
+constexpr int PMIN = 2, PMAX = 8;  // p = k + 1, 1 <= k <= 7
+constexpr int kMaxCellThreads = 256;  // block size limit of the cell kernels (register budget)
+
+// One "layer" is one cell index along one direction.  Because the map is
+// separable (x = X(xi), y = Y(eta), z = Z(zeta)), every cell integral and every
+// face integral factorises into 1D matrices per direction and layer:
+//   M  = S^T diag(w J) S        (1D mass, Gauss rule with p points)
+//   K  = D^T diag(w / J) D      (1D stiffness)
+//   Mi = M^-1                   (1D inverse mass)
+//   dL = l'(0) / J(0), dR = l'(1) / J(1)   (normal derivative at the ends)
+//   h  = extent of the layer,  t = (c_lo + c_hi) / h with c = 1/2 on an
+//        interior or periodic face and 1 on a boundary face, so that
+//        tau_e = f (k+1)^2 (t_x + t_y + t_z) is Eq. (taue) for the cell.
+// Table layout per layer, stride lstride(p):
+//   [M p*p][K p*p][Mi p*p][dL p][dR p][h][t][0][0]
+inline int lstride(int p) { return 3 * p * p + 2 * p + 4; }
+inline int lay_M(int) { return 0; }
+inline int lay_K(int p) { return p * p; }
+inline int lay_Mi(int p) { return 2 * p * p; }
+inline int lay_dL(int p) { return 3 * p * p; }
+inline int lay_dR(int p) { return 3 * p * p + p; }
+inline int lay_h(int p) { return 3 * p * p + 2 * p; }
+inline int lay_t(int p) { return 3 * p * p + 2 * p + 1; }
+
+// Geometry arguments shared by all cell kernels (passed by value).
+template <typename T>
+struct Geo {
+  int n[3];
+  int bc_lo[3], bc_hi[3];
+  int ncell;
+  const T* tab[3];  // per-direction layer tables on the device
+  T tau_scale;      // penalty factor * (k+1)^2
+};
+
+// Host-side state of one mesh.
+struct Mesh {
+  sipg_mesh_desc desc{};
+  int k = 3, p = 4;
+  double penalty = 1.0;
+  int device = 0;
+  long long ncell = 0;
+  std::vector<double> htab[3];  // host layer tables (double)
+  double* dtab64[3] = {nullptr, nullptr, nullptr};
+  float* dtab32[3] = {nullptr, nullptr, nullptr};
+  int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
+  // profiling
+  bool profile = false;
+  double prof_ms = 0.0;
+  long long prof_applies = 0;
+  long long launches = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // unread event pairs
+  // cached CG workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  ~Mesh();
+};
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+
+// ---------------------------------------------------------------- tables
+// 1D rules on [0, 1] (independent Newton iterations on Legendre polynomials).
+void gll_rule(int p, std::vector<double>& z, std::vector<double>& w);
+void gauss_rule(int n, std::vector<double>& z, std::vector<double>& w);
+// Value and derivative of all Lagrange polynomials on nodes z at point x.
+void lagrange_eval(const std::vector<double>& z, double x, std::vector<double>& val, std::vector<double>& der);
+// Analytic separable map along direction d at global reference coordinate s in [0,1].
+double map_coord(const sipg_mesh_desc& d, int dir, double s);
+// Rebuild host layer tables and upload them.
+int build_tables(Mesh& m);
+
+// ---------------------------------------------------------------- kernels
+template <typename T>
+Geo<T> make_geo(const Mesh& m);
+
+// Operator apply: y = mass_coef M x + nu (L x) [stiffness on/off]; nu_cell
+// replaces nu when not null.  If dots != null, per-block partial sums
+// (x.y, sum y, sum x) are written to dots[3 * block] and the number of blocks
+// to *nblocks.
+template <typename T>
+int launch_apply(const Mesh& m, const T* x, T* y, int ncomp, T mass_coef, T nu, const T* nu_cell, bool stiffness,
+                 double* dots, int* nblocks, cudaStream_t s);
+template <>
+int launch_apply<double>(const Mesh& m, const double* x, double* y, int ncomp, double mass_coef, double nu,
+                         const double* nu_cell, bool stiffness, double* dots, int* nblocks, cudaStream_t s);
+template <>
+int launch_apply<float>(const Mesh& m, const float* x, float* y, int ncomp, float mass_coef, float nu,
+                        const float* nu_cell, bool stiffness, double* dots, int* nblocks, cudaStream_t s);
+
+int launch_inverse_mass(const Mesh& m, const double* x, double* y, int ncomp, double* dots, const double* rdot,
+                        cudaStream_t s);
+int launch_diagonal(const Mesh& m, bool stiffness, double mass_coef, double nu, const double* nu_cell, double* diag,
+                    cudaStream_t s);
+int launch_adjoint(const Mesh& m, const double* nu_cell, const double* u, const double* lam, double* grad,
+                   cudaStream_t s);
+
+int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s, int* iters,
+             double* relres);
+
+// profiling helpers (api.cpp)
+void prof_begin(Mesh& m, cudaStream_t s, cudaEvent_t* e0);
+void prof_end(Mesh& m, cudaStream_t s, cudaEvent_t e0);
+
+int default_cpb(int p, int precision);
+
+}  // namespace sipg

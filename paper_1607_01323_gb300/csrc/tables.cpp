@@ -1,0 +1,268 @@
+// 1D bases, quadrature and the per-layer geometry tables of the separable
+// iso-parametric mapping (host code).
+//
+// Sec. 3.1: nodal Lagrange polynomials on the Legendre-Gauss-Lobatto points.
+// Sec. 5:   Gauss quadrature with n_q = k+1 points per direction; the mapping
+//           is the degree-k interpolant of the analytic map (iso-parametric);
+//           the inverse mass matrix is the tensor product of inverted 1D
+//           node-to-quadrature transforms (square because n_q = k+1).
+// Sec. 3.2, Eq. (taue): tau_e = (k+1)^2 (A(dOmega_e^Gamma)/2 + A(dOmega_e^bdy)) / V(Omega_e).
+// Sec. 7.1: the tanh grading of the wall-normal coordinate.
+#include <cmath>
+#include <cstring>
+
+#include "sipg_internal.h"
+
+namespace sipg {
+
+namespace {
+
+// P_n(t) and P_n'(t) by the three-term recurrence (long double).
+void legendre(int n, long double t, long double& P, long double& dP, long double& d2P) {
+  long double p0 = 1.0L, p1 = t;
+  if (n == 0) {
+    P = 1.0L;
+    dP = 0.0L;
+    d2P = 0.0L;
+    return;
+  }
+  for (int j = 2; j <= n; ++j) {
+    long double p2 = ((2.0L * j - 1.0L) * t * p1 - (j - 1.0L) * p0) / j;
+    p0 = p1;
+    p1 = p2;
+  }
+  P = p1;
+  // derivatives from the Legendre ODE / the identity (1-t^2) P' = n (P_{n-1} - t P_n)
+  long double one_m = 1.0L - t * t;
+  dP = n * (p0 - t * p1) / one_m;
+  d2P = (2.0L * t * dP - n * (n + 1.0L) * P) / one_m;
+}
+
+}  // namespace
+
+void gauss_rule(int n, std::vector<double>& z, std::vector<double>& w) {
+  z.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n; ++i) {
+    // Newton on P_n from the Chebyshev-like initial guess, roots in increasing order
+    long double t = -std::cos(pi * (i + 0.75L) / (n + 0.5L));
+    long double P, dP, d2P;
+    for (int it = 0; it < 100; ++it) {
+      legendre(n, t, P, dP, d2P);
+      long double dt = P / dP;
+      t -= dt;
+      if (std::fabs(dt) < 1e-19L) break;
+    }
+    legendre(n, t, P, dP, d2P);
+    z[i] = (double)(0.5L * (t + 1.0L));
+    w[i] = (double)(1.0L / ((1.0L - t * t) * dP * dP));  // 2/((1-t^2)P'^2) halved
+  }
+}
+
+void gll_rule(int p, std::vector<double>& z, std::vector<double>& w) {
+  int k = p - 1;
+  z.assign(p, 0.0);
+  w.assign(p, 0.0);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> t(p);
+  t[0] = -1.0L;
+  t[k] = 1.0L;
+  for (int i = 1; i < k; ++i) {
+    // Newton on P_k' (interior GLL nodes), started at the Chebyshev-Lobatto point
+    long double x = -std::cos(pi * i / k);
+    long double P, dP, d2P;
+    for (int it = 0; it < 100; ++it) {
+      legendre(k, x, P, dP, d2P);
+      long double dx = dP / d2P;
+      x -= dx;
+      if (std::fabs(dx) < 1e-19L) break;
+    }
+    t[i] = x;
+  }
+  for (int i = 0; i < p; ++i) {
+    long double P = 1, dP, d2P;
+    if (i == 0 || i == k) {
+      P = (i == 0 && (k % 2 == 1)) ? -1.0L : 1.0L;  // P_k(+-1) = (+-1)^k
+    } else {
+      legendre(k, t[i], P, dP, d2P);
+    }
+    z[i] = (double)(0.5L * (t[i] + 1.0L));
+    w[i] = (double)(1.0L / (k * (k + 1.0L) * P * P));
+  }
+}
+
+void lagrange_eval(const std::vector<double>& z, double x, std::vector<double>& val, std::vector<double>& der) {
+  // barycentric form: l_a(x) = (lambda_a / (x - z_a)) / sum_b lambda_b / (x - z_b)
+  const int p = (int)z.size();
+  val.assign(p, 0.0);
+  der.assign(p, 0.0);
+  std::vector<long double> lam(p, 1.0L);
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b)
+      if (b != a) lam[a] /= ((long double)z[a] - (long double)z[b]);
+  int hit = -1;
+  for (int a = 0; a < p; ++a)
+    if (std::fabs((long double)x - z[a]) < 1e-15L) hit = a;
+  if (hit >= 0) {
+    // x is node `hit`: values are a unit vector, derivatives the row of the
+    // differentiation matrix D_ij = (lambda_j / lambda_i) / (z_i - z_j), D_ii = -sum.
+    val[hit] = 1.0;
+    long double diag = 0.0L;
+    for (int b = 0; b < p; ++b) {
+      if (b == hit) continue;
+      long double d = (lam[b] / lam[hit]) / ((long double)z[hit] - (long double)z[b]);
+      der[b] = (double)d;
+      diag -= d;
+    }
+    der[hit] = (double)diag;
+    return;
+  }
+  long double s = 0.0L;
+  std::vector<long double> q(p);
+  for (int a = 0; a < p; ++a) {
+    q[a] = lam[a] / ((long double)x - z[a]);
+    s += q[a];
+  }
+  for (int a = 0; a < p; ++a) {
+    long double la = q[a] / s;
+    // l_a'(x) = l_a(x) * sum_{m != a} 1 / (x - z_m)
+    long double sd = 0.0L;
+    for (int m = 0; m < p; ++m)
+      if (m != a) sd += 1.0L / ((long double)x - z[m]);
+    val[a] = (double)la;
+    der[a] = (double)(la * sd);
+  }
+}
+
+double map_coord(const sipg_mesh_desc& d, int dir, double s) {
+  const double lo = d.lo[dir], hi = d.hi[dir];
+  if (d.map == SIPG_MAP_CHANNEL_TANH && dir == 1) {
+    double t = std::tanh(d.gamma * (2.0 * s - 1.0)) / std::tanh(d.gamma);
+    return lo + (hi - lo) * 0.5 * (1.0 + t);
+  }
+  return lo + (hi - lo) * s;
+}
+
+namespace {
+
+// Gauss-Jordan inverse of a small SPD matrix (long double).
+bool invert(int p, const std::vector<long double>& A, std::vector<long double>& Ainv) {
+  std::vector<long double> a(A);
+  Ainv.assign(p * p, 0.0L);
+  for (int i = 0; i < p; ++i) Ainv[i * p + i] = 1.0L;
+  for (int c = 0; c < p; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < p; ++r)
+      if (std::fabs(a[r * p + c]) > std::fabs(a[piv * p + c])) piv = r;
+    if (a[piv * p + c] == 0.0L) return false;
+    if (piv != c)
+      for (int j = 0; j < p; ++j) {
+        std::swap(a[c * p + j], a[piv * p + j]);
+        std::swap(Ainv[c * p + j], Ainv[piv * p + j]);
+      }
+    long double inv = 1.0L / a[c * p + c];
+    for (int j = 0; j < p; ++j) {
+      a[c * p + j] *= inv;
+      Ainv[c * p + j] *= inv;
+    }
+    for (int r = 0; r < p; ++r) {
+      if (r == c) continue;
+      long double f = a[r * p + c];
+      if (f == 0.0L) continue;
+      for (int j = 0; j < p; ++j) {
+        a[r * p + j] -= f * a[c * p + j];
+        Ainv[r * p + j] -= f * Ainv[c * p + j];
+      }
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+int build_tables(Mesh& m) {
+  const int p = m.p;
+  std::vector<double> zn, wn, zq, wq;
+  gll_rule(p, zn, wn);
+  gauss_rule(p, zq, wq);
+  // S[q][a] = l_a(x_q), D[q][a] = l_a'(x_q); end derivatives d0, d1
+  std::vector<double> S(p * p), D(p * p), d0, d1, v;
+  for (int q = 0; q < p; ++q) {
+    std::vector<double> val, der;
+    lagrange_eval(zn, zq[q], val, der);
+    for (int a = 0; a < p; ++a) {
+      S[q * p + a] = val[a];
+      D[q * p + a] = der[a];
+    }
+  }
+  lagrange_eval(zn, 0.0, v, d0);
+  lagrange_eval(zn, 1.0, v, d1);
+  const int st = lstride(p);
+  for (int dir = 0; dir < 3; ++dir) {
+    const int n = m.desc.n[dir];
+    std::vector<double>& tab = m.htab[dir];
+    tab.assign((size_t)n * st, 0.0);
+    for (int i = 0; i < n; ++i) {
+      double* L = &tab[(size_t)i * st];
+      std::vector<long double> X(p);
+      for (int a = 0; a < p; ++a) X[a] = map_coord(m.desc, dir, (i + zn[a]) / n);
+      // derivative of the degree-k interpolant of the map at the Gauss points and ends
+      std::vector<long double> J(p, 0.0L);
+      long double J0 = 0.0L, J1 = 0.0L;
+      for (int q = 0; q < p; ++q)
+        for (int a = 0; a < p; ++a) J[q] += X[a] * D[q * p + a];
+      for (int a = 0; a < p; ++a) {
+        J0 += X[a] * d0[a];
+        J1 += X[a] * d1[a];
+      }
+      for (int q = 0; q < p; ++q)
+        if (!(J[q] > 0.0L)) return fail(SIPG_EINVAL, "mapping is not monotone: degenerate cell");
+      std::vector<long double> Mm(p * p, 0.0L), Mi;
+      for (int a = 0; a < p; ++a)
+        for (int b = 0; b < p; ++b) {
+          long double sm = 0.0L, sk = 0.0L;
+          for (int q = 0; q < p; ++q) {
+            sm += (long double)wq[q] * J[q] * S[q * p + a] * S[q * p + b];
+            sk += (long double)wq[q] / J[q] * D[q * p + a] * D[q * p + b];
+          }
+          Mm[a * p + b] = sm;
+          L[lay_M(p) + a * p + b] = (double)sm;
+          L[lay_K(p) + a * p + b] = (double)sk;
+        }
+      if (!invert(p, Mm, Mi)) return fail(SIPG_EINVAL, "singular 1D mass matrix");
+      for (int j = 0; j < p * p; ++j) L[lay_Mi(p) + j] = (double)Mi[j];
+      for (int a = 0; a < p; ++a) {
+        L[lay_dL(p) + a] = (double)(d0[a] / J0);
+        L[lay_dR(p) + a] = (double)(d1[a] / J1);
+      }
+      double h = (double)(X[p - 1] - X[0]);
+      bool per = m.desc.bc_lo[dir] == SIPG_BC_PERIODIC;
+      double clo = (i == 0 && !per) ? 1.0 : 0.5;
+      double chi = (i == n - 1 && !per) ? 1.0 : 0.5;
+      L[lay_h(p)] = h;
+      L[lay_t(p)] = (clo + chi) / h;
+    }
+  }
+  // upload (double and float copies)
+  for (int dir = 0; dir < 3; ++dir) {
+    if (m.dtab64[dir]) cudaFree(m.dtab64[dir]);
+    if (m.dtab32[dir]) cudaFree(m.dtab32[dir]);
+    m.dtab64[dir] = nullptr;
+    m.dtab32[dir] = nullptr;
+    size_t cnt = m.htab[dir].size();
+    cudaError_t e = cudaMalloc(&m.dtab64[dir], cnt * sizeof(double));
+    if (e != cudaSuccess) return fail(SIPG_ENOMEM, "cudaMalloc of geometry tables failed");
+    e = cudaMalloc(&m.dtab32[dir], cnt * sizeof(float));
+    if (e != cudaSuccess) return fail(SIPG_ENOMEM, "cudaMalloc of geometry tables failed");
+    std::vector<float> f(cnt);
+    for (size_t j = 0; j < cnt; ++j) f[j] = (float)m.htab[dir][j];
+    e = cudaMemcpy(m.dtab64[dir], m.htab[dir].data(), cnt * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload geometry tables");
+    e = cudaMemcpy(m.dtab32[dir], f.data(), cnt * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload geometry tables");
+  }
+  return SIPG_OK;
+}
+
+}  // namespace sipg
