@@ -119,61 +119,75 @@ def manufactured_f(X):
     return (5 + math.pi ** 2 / 4) * np.sin(X[:, 0]) * np.cos(math.pi * X[:, 1] / 2) * np.sin(2 * X[:, 2])
 
 
-def cpu_baseline(max_seconds=25.0):
-    """The oracle as it stands (dense-quadrature element-by-element FP64 apply
-    inside its textbook Jacobi-PCG) on the same 32^3 k=4 channel problem, run
-    for a bounded number of CG iterations; returns the same metric."""
-    import numpy as np
-    from oracle.mesh import MeshSpec
-    from oracle.sipg import SIPG
-    from oracle import solvers
-    w = WORKLOAD
-    spec = MeshSpec(*w["n"], lo=w["lo"], hi=w["hi"], bc_lo=w["bc_lo"], bc_hi=w["bc_hi"], mapping=w["mapping"],
-                    gamma=w["gamma"])
-    t0 = time.time()
-    op = SIPG(spec, w["k"])
-    setup = time.time() - t0
-    X = op.node_coordinates().reshape(-1, 3)
-    b = op.mass_apply(manufactured_f(X))
-    d = op.diagonal()
-    n = b.size
-    napply = [0]
+class OracleSample:
+    """The oracle as it stands (dense-quadrature element-by-element FP64 apply)
+    on the same 32^3 k=4 channel problem, bounded: each timed unit is one
+    operator apply restricted to a fixed seeded sample of ``frac`` of the cells,
+    counted as (sampled DoFs) per second, i.e. the same DoF/s of operator apply.
+    The oracle's CG adds only vector operations around its applies."""
 
-    def A(v):
-        napply[0] += 1
-        return op.apply(v)
+    def __init__(self, frac=1.0 / 16):
+        import numpy as np
+        from oracle.mesh import MeshSpec
+        from oracle.sipg import SIPG
+        from paper_1607_01323_gb300 import inputs
+        w = WORKLOAD
+        spec = MeshSpec(*w["n"], lo=w["lo"], hi=w["hi"], bc_lo=w["bc_lo"], bc_hi=w["bc_hi"], mapping=w["mapping"],
+                        gamma=w["gamma"])
+        t0 = time.time()
+        self.op = SIPG(spec, w["k"])
+        self.setup = time.time() - t0
+        ncell = spec.ncell
+        pick = inputs.u64(0, "oracle_sample", 0, int(ncell * frac)) % np.uint64(ncell)
+        self.mask = np.zeros(ncell, dtype=bool)
+        self.mask[pick.astype(np.int64)] = True
+        self.sample_dofs = int(self.mask.sum()) * self.op.P
+        X = self.op.node_coordinates().reshape(-1, 3)
+        self.x = manufactured_f(X)
 
-    c0, t0 = time.process_time(), time.time()
-    iters = 1
-    while True:
-        napply[0] = 0
+    def step(self):
         c0, t0 = time.process_time(), time.time()
-        solvers.cg(A, b, rtol=0.0, maxit=iters, precond=lambda r: r / d)
+        self.op.apply(self.x, targets=self.mask)
         wall = time.time() - t0
-        if wall * 2 > max_seconds or iters >= 64:
-            break
-        iters *= 2
-    cpu = time.process_time() - c0
-    value = napply[0] * n / wall
-    cores = max(1, round(cpu / wall))
-    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d oracle Jacobi-PCG iterations (%d FP64 applies) of the 32^3 k=4 channel Poisson problem, "
-                      "%.1f s wall after %.1f s setup; DoF-applies per second" % (iters, napply[0], wall, setup),
-            "host_cpus": os.cpu_count()}
+        return wall, time.process_time() - c0
+
+    def describe(self, n, wall):
+        return ("%d oracle FP64 applies restricted to a seeded sample of %d of 32768 cells (%d DoF each) of the "
+                "32^3 k=4 channel Poisson operator, %.1f s wall after %.1f s oracle setup; sampled DoF per second"
+                % (n, int(self.mask.sum()), self.sample_dofs, wall, self.setup))
+
+
+def cpu_baseline(max_seconds=20.0):
+    s = OracleSample()
+    s.step()
+    walls, cpus = [], []
+    while sum(walls) < max_seconds and len(walls) < 64:
+        w, c = s.step()
+        walls.append(w)
+        cpus.append(c)
+    value = len(walls) * s.sample_dofs / sum(walls)
+    return {"value": value, "unit": UNIT, "cores": max(1, round(sum(cpus) / sum(walls))), "kind": "oracle",
+            "sample": s.describe(len(walls), sum(walls)), "host_cpus": os.cpu_count()}
 
 
 def run_reference(args):
     rank, world, _ = dist_setup(args.gpus)
     if rank != 0:
         return
-    steps = []
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(max_seconds=20.0 if i >= args.warmup else 5.0)
-        if i >= args.warmup:
-            steps.append(cb)
-    value = statistics.median(s["value"] for s in steps)
+    s = OracleSample()
+    for _ in range(args.warmup):
+        s.step()
+    walls, cpus = [], []
+    for _ in range(args.steps):
+        w, c = s.step()
+        walls.append(w)
+        cpus.append(c)
+    value = args.steps * s.sample_dofs / sum(walls)
+    steps = [{"value": value, "unit": UNIT, "cores": max(1, round(sum(cpus) / sum(walls))), "kind": "oracle",
+              "sample": s.describe(args.steps, sum(walls)), "host_cpus": os.cpu_count()}]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
+            "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": "poisson_channel_32x32x32_k4_jacobi_pcg_1e-10", "dofs": 4096000},
             "cpu_baseline": dict(steps[-1], value=value),
@@ -339,6 +353,29 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_apply_only(args):
+    """A few operator applies on the bench mesh (or --cells/--k), for ncu captures."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1607_01323_gb300 import Mesh, apply_laplace_f32, apply_laplace_f64
+    w = dict(WORKLOAD)
+    n = (args.cells,) * 3 if args.cells else w["n"]
+    k = args.k if args.k else w["k"]
+    m = Mesh(n, w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"], k=k)
+    dt = torch.float64 if args.precision == "f64" else torch.float32
+    x = torch.rand(m.n_dofs, dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    f = apply_laplace_f64 if args.precision == "f64" else apply_laplace_f32
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for i in range(args.reps):
+        ev[0].record()
+        f(m, x, y)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print("apply %s n=%s k=%d dofs=%d: %.4f ms" % (args.precision, n, k, m.n_dofs, ev[0].elapsed_time(ev[1])))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,8 +383,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply"], help="apply: only operator applies")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--cells", type=int, default=0)
+    ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "apply":
+        run_apply_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -465,6 +465,7 @@ struct Solver {
   std::vector<float> c1, c2;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
   int ev_used = 0;
+  bool capturing = false;
 
   Solver(Mesh& mm, const sipg_cg_opts& oo, int nc, cudaStream_t ss) : m(mm), o(oo), ncomp(nc), s(ss) {
     n = (long long)m.ncell * m.p * m.p * m.p * ncomp;
@@ -489,11 +490,12 @@ struct Solver {
         cudaEventCreate(&pr.second);
         evs.push_back(pr);
       }
-      cudaEventRecord(evs[ev_used].first, s);
+      // during stream capture only an "external" record becomes a graph node
+      cudaEventRecordWithFlags(evs[ev_used].first, s, capturing ? cudaEventRecordExternal : 0);
     }
     int st = launch_apply<double>(m, x, y, ncomp, cm, nu, nu_cell, true, dots, nb, s);
     if (m.profile) {
-      cudaEventRecord(evs[ev_used].second, s);
+      cudaEventRecordWithFlags(evs[ev_used].second, s, capturing ? cudaEventRecordExternal : 0);
       ++ev_used;
     }
     return st;
@@ -640,7 +642,9 @@ struct Solver {
           cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
           if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
           int cst = SIPG_OK;
+          capturing = true;
           for (int i = 0; i < chunk && cst == SIPG_OK; ++i) cst = iteration();
+          capturing = false;
           e = cudaStreamEndCapture(s, &graph);
           if (cst) {
             if (graph) cudaGraphDestroy(graph);
