@@ -215,6 +215,7 @@ def run_ours(args):
 
     w = WORKLOAD
     m = Mesh(w["n"], w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"], k=w["k"])
+    m.set_f64_arithmetic(args.f64)
     N = m.n_dofs
     p = w["k"] + 1
     X = m.node_coordinates()
@@ -328,6 +329,7 @@ def run_ours(args):
         "config": {"workload": "poisson_channel_32x32x32_k4_jacobi_pcg_1e-10", "dofs": N, "k": w["k"],
                    "gamma": w["gamma"], "rtol": RTOL, "cg_iters": iters[-1], "cuda_graph_chunk": CHECK_EVERY,
                    "l2": "256 MB buffer written between timed steps (outside the timed events)",
+                   "f64_arithmetic": args.f64,
                    "parallelism": "replicas" if world > 1 else "single"},
         "time_to_solve_s": ms_per_step / 1e3,
         "apply_f64": {"avg_ms": avg_apply_ms, "dofs_per_s": N / (avg_apply_ms / 1e3), "timed_launches": applies,
@@ -363,6 +365,7 @@ def run_apply_only(args):
     n = (args.cells,) * 3 if args.cells else w["n"]
     k = args.k if args.k else w["k"]
     m = Mesh(n, w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"], k=k)
+    m.set_f64_arithmetic(args.f64)
     dt = torch.float64 if args.precision == "f64" else torch.float32
     x = torch.rand(m.n_dofs, dtype=dt, device="cuda")
     y = torch.empty_like(x)
@@ -374,6 +377,112 @@ def run_apply_only(args):
         ev[1].record()
         torch.cuda.synchronize()
         print("apply %s n=%s k=%d dofs=%d: %.4f ms" % (args.precision, n, k, m.n_dofs, ev[0].elapsed_time(ev[1])))
+
+
+def _timed(fn, reps=3):
+    """Median wall time (s) of fn() bracketed by device synchronisation."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts), out
+
+
+def run_config(args):
+    """Timings of the other workload configurations (one JSON line each):
+    c3: 3-component viscous Helmholtz on the 64^3 k=3 channel (apply, autotune,
+        graph-captured CG with M^-1 and Jacobi);
+    c4: Neumann-channel Poisson 48^3 k=5, FP32 Chebyshev(4) + FP64 flexible CG
+        versus plain FP64 Jacobi CG;
+    c5: adjoint gradient on the 32^3 k=3 channel with per-cell viscosity."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1607_01323_gb300 import (Mesh, apply_helmholtz_f64, apply_laplace_f32, apply_laplace_f64,
+                                        apply_mass_f64, autotune, cg_solve, inputs)
+    w = WORKLOAD
+    out = {"workload": args.workload}
+    if args.workload == "c3":
+        m = Mesh((64, 64, 64), w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping="channel", gamma=1.8, k=3)
+        N = m.n_dofs
+        cm, nu = 1.5 / 1e-3, 1 / 180
+        X = m.node_coordinates()
+        u_in = np.concatenate([(1 - X[:, 1] ** 2) + 0.1 * inputs.normal(0, "ux", N),
+                               0.1 * inputs.normal(0, "uy", N), 0.1 * inputs.normal(0, "uz", N)])
+        u = torch.tensor(u_in, device="cuda")
+        y = torch.empty_like(u)
+        out["cpb_default"] = m.cells_per_block(0)
+        t_def, _ = _timed(lambda: apply_helmholtz_f64(m, u, cm, nu, y=y), reps=5)
+        out["cpb_autotuned"] = autotune(m, 0)
+        t_apply, _ = _timed(lambda: apply_helmholtz_f64(m, u, cm, nu, y=y), reps=5)
+        out["apply_f64"] = {"ms_default_cpb": 1e3 * t_def, "ms": 1e3 * t_apply, "dofs": 3 * N,
+                            "dofs_per_s": 3 * N / t_apply}
+        rhs = cm * apply_mass_f64(m, u)
+        for pc in ("invmass", "jacobi"):
+            x = torch.zeros_like(rhs)
+            for graph in (1, 0):
+                t, (x, res) = _timed(lambda: cg_solve(m, rhs, torch.zeros_like(rhs), op="helmholtz",
+                                                      mass_coef=cm, nu=nu, precond=pc, rtol=1e-10,
+                                                      use_graph=graph), reps=3)
+                out["solve_%s_%s" % (pc, "graph" if graph else "loop")] = {
+                    "s": t, "iters": res.iters, "relres": res.relres,
+                    "dof_applies_per_s": 3 * N * (res.iters + 1) / t}
+    elif args.workload == "c4":
+        m = Mesh((48, 48, 48), w["lo"], w["hi"], ("periodic", "neumann", "periodic"),
+                 ("periodic", "neumann", "periodic"), mapping="channel", gamma=1.8, k=5)
+        N = m.n_dofs
+        b = inputs.uniform(0, "b", N)
+        b -= b.mean()
+        bt = torch.tensor(b, device="cuda")
+        x32 = bt.float()
+        y32 = torch.empty_like(x32)
+        y64 = torch.empty_like(bt)
+        t32, _ = _timed(lambda: apply_laplace_f32(m, x32, y32), reps=5)
+        t64, _ = _timed(lambda: apply_laplace_f64(m, bt, y64), reps=5)
+        out["apply_f32"] = {"ms": 1e3 * t32, "dofs_per_s": N / t32}
+        out["apply_f64"] = {"ms": 1e3 * t64, "dofs_per_s": N / t64}
+        tc, (xc, rc) = _timed(lambda: cg_solve(m, bt, precond="cheb_f32", cheb_degree=4, zero_mean=1,
+                                                rtol=1e-10), reps=2)
+        tj, (xj, rj) = _timed(lambda: cg_solve(m, bt, precond="jacobi", zero_mean=1, rtol=1e-10), reps=2)
+        d = (xc - xc.mean()) - (xj - xj.mean())
+        out["mixed_cheb4_fcg"] = {"s": tc, "iters": rc.iters, "relres": rc.relres}
+        out["plain_f64_jacobi_cg"] = {"s": tj, "iters": rj.iters, "relres": rj.relres}
+        out["speedup"] = tj / tc
+        out["rel_diff_solutions"] = (torch.linalg.norm(d) / torch.linalg.norm(xj - xj.mean())).item()
+    elif args.workload == "c5":
+        from paper_1607_01323_gb300.autograd import helmholtz_solve, mass_norm_loss
+        m = Mesh((32, 32, 32), w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping="channel", gamma=1.8, k=3)
+        cm = 1500.0
+        nu = torch.tensor(np.exp(0.5 * inputs.normal(0, "xi", m.ncell)) / 180.0, device="cuda")
+        X = m.node_coordinates()
+        fc = np.sin(X[:, 0]) * np.cos(math.pi * X[:, 1] / 2) * np.sin(2 * X[:, 2])
+        ph = 2 * math.pi * (0.5 * (inputs.uniform(0, "phase", 2) + 1))
+        ut = torch.tensor(np.cos(math.pi * X[:, 1] / 2) * (1 + 0.5 * np.sin(X[:, 0] + ph[0]) *
+                                                           np.cos(X[:, 2] + ph[1])), device="cuda")
+        f = apply_mass_f64(m, torch.tensor(fc, device="cuda"))
+
+        def fwd():
+            return mass_norm_loss(m, helmholtz_solve(m, nu, f, cm, rtol=1e-10), ut)
+
+        def fwd_bwd():
+            nu_t = nu.clone().requires_grad_(True)
+            J = mass_norm_loss(m, helmholtz_solve(m, nu_t, f, cm, rtol=1e-10), ut)
+            J.backward()
+            return nu_t.grad
+
+        t_f, _ = _timed(fwd, reps=3)
+        t_fb, g = _timed(fwd_bwd, reps=3)
+        out["forward_s"] = t_f
+        out["forward_backward_s"] = t_fb
+        out["backward_over_forward"] = (t_fb - t_f) / t_f
+        out["finite_difference_estimate_s"] = 2 * m.ncell * t_f
+        out["grad_norm"] = torch.linalg.norm(g).item()
+    print(json.dumps(out))
 
 
 def main():
@@ -388,9 +497,15 @@ def main():
     ap.add_argument("--cells", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--f64", default="native", choices=["native", "double_float"],
+                    help="arithmetic of the FP64 operator (double_float: FP32 pairs on the FP32 pipes)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 (default) is the bench step; c3-c5 print timings of the other configurations")
     args = ap.parse_args()
     if args.mode == "apply":
         run_apply_only(args)
+    elif args.workload != "c2":
+        run_config(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -60,6 +60,7 @@ typedef enum {
 typedef enum { SIPG_BC_PERIODIC = 0, SIPG_BC_DIRICHLET = 1, SIPG_BC_NEUMANN = 2 } sipg_bc;
 typedef enum { SIPG_MAP_AFFINE = 0, SIPG_MAP_CHANNEL_TANH = 1 } sipg_map;
 typedef enum { SIPG_OP_LAPLACE = 0, SIPG_OP_HELMHOLTZ = 1 } sipg_op;
+typedef enum { SIPG_F64_NATIVE = 0, SIPG_F64_DOUBLE_FLOAT = 1 } sipg_f64_arith;
 typedef enum {
   SIPG_PC_NONE = 0,
   SIPG_PC_JACOBI = 1,     /* z = diag(A)^-1 r (Sec. 5.1: the diagonal computed once)   */
@@ -196,6 +197,18 @@ int sipg_adjoint_grad_nu(const sipg_mesh* mesh, const double* nu_cell, const dou
  * If cache_path is not NULL the choice is read from / appended to that text
  * file (one "key value" line per (k, precision, map, mesh size)). */
 int sipg_autotune(sipg_mesh* mesh, int precision, const char* cache_path);
+
+/* Arithmetic of the FP64 operator entry points for a uniform viscosity
+ * (sipg_apply_laplace_f64, sipg_apply_helmholtz_f64 with nu_cell == NULL, and
+ * the operator inside sipg_cg_solve).  SIPG_F64_NATIVE (default) computes in
+ * FP64.  SIPG_F64_DOUBLE_FLOAT keeps the FP64 data in memory but evaluates the
+ * sum-factorised operator in double-float arithmetic (pairs of FP32 with exact
+ * product errors and TwoSum, about 2^-46 relative per operation) on the FP32
+ * pipes, which issue 64 times the FP64 rate on GB300; results stay within the
+ * FP64 parity tolerance (1e-12 of ||A|| ||x||).  The per-cell-viscosity
+ * operator, the mass, inverse-mass and adjoint kernels always use FP64. */
+int sipg_set_f64_arithmetic(sipg_mesh* mesh, int mode);
+int sipg_get_f64_arithmetic(const sipg_mesh* mesh, int* mode);
 
 /* Cells per block currently used for a precision (host output). */
 int sipg_get_cells_per_block(const sipg_mesh* mesh, int precision, int* cpb);

@@ -116,6 +116,12 @@ class Mesh:
         L.check(L.lib().sipg_penalty_values(self._h, out.ctypes.data_as(C.c_void_p)))
         return out
 
+    def set_f64_arithmetic(self, mode):
+        """'native' (FP64) or 'double_float' (FP32 pairs) for the FP64 operator
+        with a uniform viscosity."""
+        L.check(L.lib().sipg_set_f64_arithmetic(self._h, {"native": 0, "double_float": 1}[mode]))
+        self.f64_arithmetic = mode
+
     def cells_per_block(self, precision=0):
         v = C.c_int()
         L.check(L.lib().sipg_get_cells_per_block(self._h, int(precision), C.byref(v)))

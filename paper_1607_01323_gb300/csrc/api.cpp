@@ -7,6 +7,7 @@
 #include <fstream>
 #include <sstream>
 #include <string>
+#include <type_traits>
 
 #include "sipg_internal.h"
 
@@ -32,6 +33,8 @@ Mesh::~Mesh() {
     if (dtab64[d]) cudaFree(dtab64[d]);
     if (dtab32[d]) cudaFree(dtab32[d]);
   }
+  for (int d = 0; d < 3; ++d)
+    if (dtabdf[d]) cudaFree(dtabdf[d]);
   if (ws) cudaFree(ws);
   for (auto& pr : pending) {
     cudaEventDestroy(pr.first);
@@ -49,16 +52,19 @@ Geo<T> make_geo(const Mesh& m) {
   }
   g.ncell = (int)m.ncell;
   for (int d = 0; d < 3; ++d) {
-    if (sizeof(T) == 8)
+    if (std::is_same<T, double>::value)
       g.tab[d] = reinterpret_cast<const T*>(m.dtab64[d]);
-    else
+    else if (std::is_same<T, float>::value)
       g.tab[d] = reinterpret_cast<const T*>(m.dtab32[d]);
+    else
+      g.tab[d] = reinterpret_cast<const T*>(m.dtabdf[d]);
   }
-  g.tau_scale = (T)(m.penalty * (m.k + 1) * (m.k + 1));
+  g.tau_scale = T(m.penalty * (m.k + 1) * (m.k + 1));
   return g;
 }
 template Geo<double> make_geo<double>(const Mesh&);
 template Geo<float> make_geo<float>(const Mesh&);
+template Geo<dfl> make_geo<dfl>(const Mesh&);
 
 int default_cpb(int p, int precision) {
   (void)precision;
@@ -217,8 +223,16 @@ int sipg_set_penalty(sipg_mesh* m, double f) {
   int st;
   if ((st = check_mesh(m))) return st;
   if (!(f > 0.0) || !std::isfinite(f)) return fail(SIPG_EINVAL, "penalty factor must be > 0");
+  if ((st = set_device(*m))) return st;
+  cudaDeviceSynchronize();  // the tables hold the penalty shares: no launch may still read them
+  const double f0 = m->penalty;
   m->penalty = f;
-  return SIPG_OK;
+  st = build_tables(*m);
+  if (st) {
+    m->penalty = f0;
+    build_tables(*m);
+  }
+  return st;
 }
 
 int sipg_n_dofs(const sipg_mesh* m, long long* n) {
@@ -403,6 +417,22 @@ int sipg_adjoint_grad_nu(const sipg_mesh* mc, const double* nu_cell, const doubl
   Mesh& m = const_cast<sipg_mesh&>(*mc);
   if ((st = set_device(m))) return st;
   return launch_adjoint(m, nu_cell, u, lam, grad, (cudaStream_t)stream);
+}
+
+int sipg_set_f64_arithmetic(sipg_mesh* m, int mode) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (mode != SIPG_F64_NATIVE && mode != SIPG_F64_DOUBLE_FLOAT) return fail(SIPG_EINVAL, "unknown FP64 arithmetic");
+  m->f64_arith = mode;
+  return SIPG_OK;
+}
+
+int sipg_get_f64_arithmetic(const sipg_mesh* m, int* mode) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!mode) return fail(SIPG_EINVAL, "NULL output");
+  *mode = m->f64_arith;
+  return SIPG_OK;
 }
 
 int sipg_get_cells_per_block(const sipg_mesh* m, int precision, int* cpb) {

@@ -26,14 +26,36 @@
 // its own outputs, so there are no atomics and the result is deterministic.
 #pragma once
 
+#include "dfloat.cuh"
 #include "sipg_internal.h"
 
 namespace sipg {
 
+// storage <-> compute conversions (identity unless FP64 data is computed in
+// double-float)
+template <typename T, typename S>
+__device__ __forceinline__ T cvt_in(S v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ dfl cvt_in<dfl, double>(double v) {
+  return df_from_double(v);
+}
+template <typename S, typename T>
+__device__ __forceinline__ S cvt_out(T v) {
+  return (S)v;
+}
+template <>
+__device__ __forceinline__ double cvt_out<double, dfl>(dfl v) {
+  return df_to_double(v);
+}
+
 template <int P>
 struct LayerOff {
-  static constexpr int M = 0, K = P * P, Mi = 2 * P * P, dL = 3 * P * P, dR = 3 * P * P + P, h = 3 * P * P + 2 * P,
-                       t = 3 * P * P + 2 * P + 1, stride = 3 * P * P + 2 * P + 4;
+  static constexpr int M = 0, K = P * P, Mi = 2 * P * P, Kc = 3 * P * P, dL = 4 * P * P, dR = 4 * P * P + P,
+                       dLh = 4 * P * P + 2 * P, dRh = 4 * P * P + 3 * P, h = 4 * P * P + 4 * P,
+                       t = 4 * P * P + 4 * P + 1, ts = 4 * P * P + 4 * P + 2, dTL = 4 * P * P + 4 * P + 3,
+                       dTR = 4 * P * P + 4 * P + 4, stride = 4 * P * P + 4 * P + 8;
 };
 
 // Neighbour across side (0 = low, 1 = high) of direction dir.  kind: 0 interior
@@ -390,6 +412,191 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
         d_y += (double)out[a];
         d_x += (double)ux[a];
       }
+    }
+  }
+  if (dots) block_reduce3(d_xy, d_y, d_x, dots + 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
+}
+
+// Uniform-viscosity line operator (unit viscosity; the caller scales): the own
+// cell's part of the 1D stiffness and of both faces' consistency terms is the
+// precombined matrix Kc; what remains per interior face is the neighbour's
+// half normal derivative, the jump penalty tau_F [u] and the scatter of the
+// neighbour's trace; a Dirichlet face adds 2 tau_e u.
+template <typename T, int P>
+__device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* __restrict__ L, int kindL,
+                                          const T (&uL)[P], const T* __restrict__ LL, T tauFL, int kindR,
+                                          const T (&uR)[P], const T* __restrict__ LR, T tauFR, T tau2e) {
+  using O = LayerOff<P>;
+  matvec<T, P>(w, L + O::Kc, u);
+  if (kindR == 0) {
+    T gn = T(0);
+#pragma unroll
+    for (int a = 0; a < P; ++a) gn = fma(LR[O::dLh + a], uR[a], gn);
+    const T J = u[P - 1] - uR[0];
+    w[P - 1] += fma(tauFR, J, -gn);
+    const T ur = uR[0];
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[a] = fma(L[O::dRh + a], ur, w[a]);
+  } else if (kindR == SIPG_BC_DIRICHLET) {
+    w[P - 1] = fma(tau2e, u[P - 1], w[P - 1]);
+  }
+  if (kindL == 0) {
+    T gn = T(0);
+#pragma unroll
+    for (int a = 0; a < P; ++a) gn = fma(LL[O::dRh + a], uL[a], gn);
+    const T J = uL[P - 1] - u[0];
+    w[0] += fma(-tauFL, J, gn);
+    const T ul = -uL[P - 1];
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[a] = fma(L[O::dLh + a], ul, w[a]);
+  } else if (kindL == SIPG_BC_DIRICHLET) {
+    w[0] = fma(tau2e, u[0], w[0]);
+  }
+}
+
+// y = scale * (L x + mass_rel M x) for a uniform viscosity: scale = nu,
+// mass_rel = mass_coef / nu (Laplace: scale 1, mass_rel 0).  Same phases as
+// apply_kernel with the precombined line operator.
+template <typename T, typename S, int P>
+__device__ __forceinline__ void load_line_global_cvt(T (&v)[P], const S* __restrict__ base, int start, int step) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) v[a] = cvt_in<T, S>(__ldg(base + start + a * step));
+}
+
+template <typename T, typename S, int P>
+__global__ void __launch_bounds__(kMaxCellThreads) apply_uniform_kernel(Geo<T> g, const S* __restrict__ x,
+                                                                        S* __restrict__ y, int cpb, T mass_rel,
+                                                                        T scale, int do_scale, int do_mass,
+                                                                        double* __restrict__ dots) {
+  using O = LayerOff<P>;
+  constexpr int P2 = P * P, P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);
+  T* s1 = su + cpb * P3;
+  T* s2 = s1 + cpb * P3;
+  const int cs = threadIdx.x / P2;
+  const int t = threadIdx.x - cs * P2;
+  const int ti = t % P, tj = t / P;
+  const long long cell0 = (long long)blockIdx.x * cpb;
+  const int e = (int)(cell0 + cs);
+  const bool active = cs < cpb && e < g.ncell;  // blocks are rounded up to whole warps
+  const long long cbase = (long long)blockIdx.y * g.ncell * P3;
+  const S* __restrict__ xc = x + cbase;
+  {
+    const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
+    const S* xb = xc + cell0 * P3;
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx]);
+  }
+  __syncthreads();
+  T* us = su + cs * P3;
+  T* w1 = s1 + cs * P3;
+  T* w2 = s2 + cs * P3;
+  int id[3] = {0, 0, 0};
+  T tau_e = T(0);
+  if (active) {
+    id[0] = e % g.n[0];
+    id[1] = (e / g.n[0]) % g.n[1];
+    id[2] = e / (g.n[0] * g.n[1]);
+    tau_e = g.tab[0][id[0] * O::stride + O::ts] + g.tab[1][id[1] * O::stride + O::ts] +
+            g.tab[2][id[2] * O::stride + O::ts];
+  }
+  const T tau2e = tau_e + tau_e;
+  T ux[P];
+  if (active) {
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      int start, step;
+      line_geom<P>(dir, ti, tj, start, step);
+      const T* L = g.tab[dir] + id[dir] * O::stride;
+      int nbL, nbR, kL, kR, jl, jr;
+      face_neighbor(g, dir, 0, id[dir], e, nbL, kL, jl);
+      face_neighbor(g, dir, 1, id[dir], e, nbR, kR, jr);
+      T u[P], uL[P], uR[P], w[P];
+      load_line<T, P>(u, us, start, step);
+      if (dir == 0) {
+#pragma unroll
+        for (int a = 0; a < P; ++a) ux[a] = u[a];
+      }
+      if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step);
+      if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step);
+      line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
+                      kR == 0 ? g.tab[dir] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
+      store_line<T, P>(dir == 0 ? w1 : w2, w, start, step);
+    }
+  }
+  __syncthreads();
+  if (active) {
+    int start, step;
+    line_geom<P>(2, ti, tj, start, step);
+    const T* L = g.tab[2] + id[2] * O::stride;
+    int nbL, nbR, kL, kR, jl, jr;
+    face_neighbor(g, 2, 0, id[2], e, nbL, kL, jl);
+    face_neighbor(g, 2, 1, id[2], e, nbR, kR, jr);
+    T u[P], uL[P], uR[P], w[P], v1[P], v2[P], a1[P], a2[P];
+    load_line<T, P>(u, us, start, step);
+    if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step);
+    if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step);
+    line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
+                    kR == 0 ? g.tab[2] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
+    if (do_mass) {
+      T mu[P];
+      matvec<T, P>(mu, L + O::M, u);
+#pragma unroll
+      for (int a = 0; a < P; ++a) w[a] = fma(mass_rel, mu[a], w[a]);
+    }
+    load_line<T, P>(v1, w1, start, step);
+    load_line<T, P>(v2, w2, start, step);
+    matvec<T, P>(a1, L + O::M, v1);
+    matvec<T, P>(a2, L + O::M, v2);
+    store_line<T, P>(us, w, start, step);
+    store_line<T, P>(w1, a1, start, step);
+    store_line<T, P>(w2, a2, start, step);
+  }
+  __syncthreads();
+  if (active) {
+    int start, step;
+    line_geom<P>(1, ti, tj, start, step);
+    const T* My = g.tab[1] + id[1] * O::stride + O::M;
+    T v[P], r1[P], r2[P], a2[P];
+    load_line<T, P>(v, w1, start, step);
+    matvec<T, P>(r1, My, v);
+    load_line<T, P>(v, us, start, step);
+    matvec<T, P>(r2, My, v);
+    load_line<T, P>(a2, w2, start, step);
+#pragma unroll
+    for (int a = 0; a < P; ++a) r2[a] += a2[a];
+    store_line<T, P>(w1, r1, start, step);
+    store_line<T, P>(w2, r2, start, step);
+  }
+  __syncthreads();
+  double d_xy = 0.0, d_y = 0.0, d_x = 0.0;
+  if (active) {
+    int start, step;
+    line_geom<P>(0, ti, tj, start, step);
+    const T* Mx = g.tab[0] + id[0] * O::stride + O::M;
+    T v[P], out[P], r1[P];
+    load_line<T, P>(v, w2, start, step);
+    matvec<T, P>(out, Mx, v);
+    load_line<T, P>(r1, w1, start, step);
+    S* yo = y + cbase + (long long)e * P3 + start;
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      out[a] += r1[a];
+      if (do_scale) out[a] *= scale;
+      yo[a] = cvt_out<S, T>(out[a]);
+    }
+    if (dots) {
+      // line sums in the compute type, one conversion per line
+      T sxy(0), sy(0), sx(0);
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        sxy = fma(out[a], ux[a], sxy);
+        sy += out[a];
+        sx += ux[a];
+      }
+      d_xy = cvt_out<double, T>(sxy);
+      d_y = cvt_out<double, T>(sy);
+      d_x = cvt_out<double, T>(sx);
     }
   }
   if (dots) block_reduce3(d_xy, d_y, d_x, dots + 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));

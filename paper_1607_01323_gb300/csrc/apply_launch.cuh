@@ -2,6 +2,8 @@
 // apply_f64.cu and apply_f32.cu so that the two compile in parallel).
 #pragma once
 
+#include <type_traits>
+
 #include "apply.cuh"
 
 namespace sipg {
@@ -16,11 +18,37 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
   const int threads = (cpb * P * P + 31) / 32 * 32;  // whole warps (the block reduction shuffles full warps)
   const size_t smem = (size_t)3 * cpb * P * P * P * sizeof(T);
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
+  const bool uniform = stiff && nu_cell == nullptr;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(apply_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = uniform ? cudaFuncSetAttribute(apply_uniform_kernel<T, T, P>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                            : cudaFuncSetAttribute(apply_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
   }
-  apply_kernel<T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm, nu, nu_cell, stiff ? 1 : 0, dots);
+  if (uniform) {
+    // y = nu (L x + (mass_coef / nu) M x)
+    const int do_scale = nu != T(1) ? 1 : 0, do_mass = cm != T(0) ? 1 : 0;
+    if constexpr (std::is_same<T, double>::value) {
+      if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
+        const Geo<dfl> gd = make_geo<dfl>(m);
+        if (smem > 48 * 1024) {
+          cudaError_t e = cudaFuncSetAttribute(apply_uniform_kernel<dfl, double, P>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
+        }
+        apply_uniform_kernel<dfl, double, P><<<grid, threads, smem, s>>>(gd, x, y, cpb, dfl(cm / nu), dfl(nu),
+                                                                         do_scale, do_mass, dots);
+        if (nblocks) *nblocks = (int)(grid.x * grid.y);
+        const_cast<Mesh&>(m).launches++;
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch");
+      }
+    }
+    apply_uniform_kernel<T, T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm / nu, nu, do_scale, do_mass, dots);
+  } else {
+    apply_kernel<T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm, nu, nu_cell, stiff ? 1 : 0, dots);
+  }
   if (nblocks) *nblocks = (int)(grid.x * grid.y);
   const_cast<Mesh&>(m).launches++;
   cudaError_t e = cudaGetLastError();

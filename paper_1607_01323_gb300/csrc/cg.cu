@@ -154,7 +154,7 @@ __global__ void k_init_precond(const Scalars* __restrict__ sc, long long n, doub
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double ri = r[i] - mean;
     r[i] = ri;
-    const double zi = diag ? ri / diag[i] : ri;
+    const double zi = diag ? ri * diag[i] : ri;
     if (z != r) z[i] = zi;
     rr += ri * ri;
     rz += ri * zi;
@@ -182,29 +182,41 @@ __global__ void k_alpha(Scalars* sc, const double* __restrict__ part, int nb, in
   }
 }
 
-// x += alpha p; r -= alpha (Ap - mean); Jacobi/none: z = D^-1 r.
-// partials: (r.r, r.z, z.(Ap - mean)) -- the last two only when z is formed here.
-__global__ void k_update(const Scalars* __restrict__ sc, long long n, double* __restrict__ x,
-                         double* r, const double* __restrict__ p, const double* __restrict__ ap,
-                         double* z, const double* __restrict__ diag, int form_z,
-                         double* __restrict__ part) {
+// x += alpha p; r -= alpha (Ap - mean); Jacobi/none: z = D^-1 r (diag holds
+// the inverse diagonal).  partials: (r.r, r.z, z.(Ap - mean)) -- the last two
+// only when z is formed here, the last only for the flexible beta.  Every FP64
+// operation counts on this GPU (2 FP64 FMA/clk/SM): the mean subtraction and
+// z.q are skipped when not needed.
+template <bool FORM_Z, bool ZERO_MEAN, bool ZQ>
+__global__ void k_update(const Scalars* __restrict__ sc, long long n, double* __restrict__ x, double* r,
+                         const double* __restrict__ p, const double* __restrict__ ap, double* z,
+                         const double* __restrict__ diag, double* __restrict__ part) {
   if (sc->done) return;
   const double alpha = sc->alpha, mean = sc->mean;
   double rr = 0.0, rz = 0.0, zq = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double q = ap[i] - mean;
+    const double q = ZERO_MEAN ? ap[i] - mean : ap[i];
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q, r[i]);
     r[i] = ri;
-    rr += ri * ri;
-    if (form_z) {
-      const double zi = diag ? ri / diag[i] : ri;
+    rr = fma(ri, ri, rr);
+    if (FORM_Z) {
+      const double zi = diag ? ri * diag[i] : ri;
       if (z != r) z[i] = zi;
-      rz += ri * zi;
-      zq += zi * q;
+      rz = fma(ri, zi, rz);
+      if (ZQ) zq = fma(zi, q, zq);
     }
   }
   block_partial3(rr, rz, zq, part);
+}
+
+using UpdateFn = void (*)(const Scalars*, long long, double*, double*, const double*, const double*, double*,
+                          const double*, double*);
+
+UpdateFn pick_update(bool form_z, bool zero_mean, bool zq) {
+  if (!form_z) return zero_mean ? k_update<false, true, false> : k_update<false, false, false>;
+  if (zero_mean) return zq ? k_update<true, true, true> : k_update<true, true, false>;
+  return zq ? k_update<true, false, true> : k_update<true, false, false>;
 }
 
 // beta and the convergence test.  part1: (r.r, r.z, z.q) from k_update, or
@@ -342,14 +354,16 @@ __global__ void k_cheb_finish(const Scalars* __restrict__ sc, long long n, const
   block_partial3(rz, zq, 0.0, part);
 }
 
-__global__ void k_inv_f32(long long n, const double* __restrict__ d, float* __restrict__ dinv) {
+__global__ void k_inv_f32(long long n, const double* __restrict__ dinv64, float* __restrict__ dinv) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    dinv[i] = (float)(1.0 / d[i]);
+    dinv[i] = (float)dinv64[i];
 }
 
-__global__ void k_copy_rep(long long n, long long per, const double* __restrict__ src, double* __restrict__ dst) {
+// dst[i] = 1 / src[i mod per]: the inverse diagonal, replicated per component
+// (FP64 division is expensive on this GPU: it is done once per solve)
+__global__ void k_inv_rep(long long n, long long per, const double* __restrict__ src, double* __restrict__ dst) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    dst[i] = src[i % per];
+    dst[i] = 1.0 / src[i % per];
 }
 
 __global__ void k_fill(long long n, double v, double* __restrict__ dst) {
@@ -553,7 +567,9 @@ struct Solver {
     const bool sep = separate_precond();
     const double* dg = o.precond == SIPG_PC_JACOBI ? w.diag : nullptr;
     double* z = (o.precond == SIPG_PC_NONE) ? w.r : w.z;
-    k_update<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, xcur, w.r, w.p, w.ap, z, dg, sep ? 0 : 1, w.part1);
+    const int flex = o.precond == SIPG_PC_CHEB_F32 || (o.flexible && o.precond != SIPG_PC_INVMASS);
+    pick_update(!sep, o.zero_mean != 0, flex != 0)<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, xcur, w.r, w.p, w.ap,
+                                                                                      z, dg, w.part1);
     if ((st = launched())) return st;
     int nb2 = kVecBlocks;
     if (o.precond == SIPG_PC_INVMASS) {
@@ -565,7 +581,6 @@ struct Solver {
       if ((st = cheb_apply(w.z, w.r, w.ap, w.sc))) return st;
     }
     // flexible beta needs z.(Ap - mean); the inverse-mass path uses the standard beta
-    const int flex = o.precond == SIPG_PC_CHEB_F32 || (o.flexible && o.precond != SIPG_PC_INVMASS);
     k_beta<<<1, kRedThreads, 0, s>>>(w.sc, w.part1, kVecBlocks, sep ? w.part2 : nullptr, nb2, flex);
     if ((st = launched())) return st;
     k_pupdate<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, w.p, z, 0);
@@ -709,7 +724,7 @@ int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int nco
   const double* nuc = helm ? o.nu_cell : nullptr;
   if (o.precond == SIPG_PC_JACOBI || o.precond == SIPG_PC_CHEB_F32) {
     if ((st = launch_diagonal(m, true, cm, nu, nuc, w.xs, s))) return st;
-    k_copy_rep<<<kVecBlocks, kVecThreads, 0, s>>>(n, N, w.xs, w.diag);
+    k_inv_rep<<<kVecBlocks, kVecThreads, 0, s>>>(n, N, w.xs, w.diag);
     if ((st = S.launched())) return st;
   }
   if (o.precond == SIPG_PC_CHEB_F32) {
@@ -777,5 +792,6 @@ int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int nco
     default: return fail(SIPG_EINVAL, "CG ended in an unknown state");
   }
 }
+
 
 }  // namespace sipg

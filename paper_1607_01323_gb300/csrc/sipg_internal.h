@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "sipg.h"
 
 namespace sipg {
@@ -24,16 +25,31 @@ constexpr int kMaxCellThreads = 256;  // block size limit of the cell kernels (r
 //   h  = extent of the layer,  t = (c_lo + c_hi) / h with c = 1/2 on an
 //        interior or periodic face and 1 on a boundary face, so that
 //        tau_e = f (k+1)^2 (t_x + t_y + t_z) is Eq. (taue) for the cell.
+// For the uniform-viscosity kernel the own-face consistency terms of a layer are
+// folded into one matrix and the averages' 1/2 into the derivative vectors:
+//   Kc  = K - c_hi (e_R dR^T + dR e_R^T) + c_lo (e_L dL^T + dL e_L^T)
+//         (c = 1/2 on an interior or periodic face, 1 on a Dirichlet face,
+//         0 on a Neumann face),
+//   dLh = dL / 2, dRh = dR / 2,
+//   ts  = f (k+1)^2 t (this layer's share of tau_e),
+//   dTL, dTR = max(0, ts of the low / high neighbour layer - ts), so that the
+//   face penalty max(tau_e, tau_neighbour) of Eq. (tau) is tau_e + dT.
 // Table layout per layer, stride lstride(p):
-//   [M p*p][K p*p][Mi p*p][dL p][dR p][h][t][0][0]
-inline int lstride(int p) { return 3 * p * p + 2 * p + 4; }
+//   [M p*p][K p*p][Mi p*p][Kc p*p][dL p][dR p][dLh p][dRh p][h][t][ts][dTL][dTR][0][0][0]
+inline int lstride(int p) { return 4 * p * p + 4 * p + 8; }
 inline int lay_M(int) { return 0; }
 inline int lay_K(int p) { return p * p; }
 inline int lay_Mi(int p) { return 2 * p * p; }
-inline int lay_dL(int p) { return 3 * p * p; }
-inline int lay_dR(int p) { return 3 * p * p + p; }
-inline int lay_h(int p) { return 3 * p * p + 2 * p; }
-inline int lay_t(int p) { return 3 * p * p + 2 * p + 1; }
+inline int lay_Kc(int p) { return 3 * p * p; }
+inline int lay_dL(int p) { return 4 * p * p; }
+inline int lay_dR(int p) { return 4 * p * p + p; }
+inline int lay_dLh(int p) { return 4 * p * p + 2 * p; }
+inline int lay_dRh(int p) { return 4 * p * p + 3 * p; }
+inline int lay_h(int p) { return 4 * p * p + 4 * p; }
+inline int lay_t(int p) { return 4 * p * p + 4 * p + 1; }
+inline int lay_ts(int p) { return 4 * p * p + 4 * p + 2; }
+inline int lay_dTL(int p) { return 4 * p * p + 4 * p + 3; }
+inline int lay_dTR(int p) { return 4 * p * p + 4 * p + 4; }
 
 // Geometry arguments shared by all cell kernels (passed by value).
 template <typename T>
@@ -55,6 +71,8 @@ struct Mesh {
   std::vector<double> htab[3];  // host layer tables (double)
   double* dtab64[3] = {nullptr, nullptr, nullptr};
   float* dtab32[3] = {nullptr, nullptr, nullptr};
+  dfl* dtabdf[3] = {nullptr, nullptr, nullptr};  // double-float copies (hi, lo)
+  int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
   // profiling
   bool profile = false;

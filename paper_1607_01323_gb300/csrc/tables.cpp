@@ -242,14 +242,45 @@ int build_tables(Mesh& m) {
       double chi = (i == n - 1 && !per) ? 1.0 : 0.5;
       L[lay_h(p)] = h;
       L[lay_t(p)] = (clo + chi) / h;
+      // own-face consistency weights of the precombined matrix Kc
+      const double wlo = (i == 0 && !per) ? (m.desc.bc_lo[dir] == SIPG_BC_DIRICHLET ? 1.0 : 0.0) : 0.5;
+      const double whi = (i == n - 1 && !per) ? (m.desc.bc_hi[dir] == SIPG_BC_DIRICHLET ? 1.0 : 0.0) : 0.5;
+      const double* dL = L + lay_dL(p);
+      const double* dR = L + lay_dR(p);
+      for (int a = 0; a < p; ++a)
+        for (int b = 0; b < p; ++b) {
+          double v = L[lay_K(p) + a * p + b];
+          v -= whi * ((a == p - 1 ? dR[b] : 0.0) + (b == p - 1 ? dR[a] : 0.0));
+          v += wlo * ((a == 0 ? dL[b] : 0.0) + (b == 0 ? dL[a] : 0.0));
+          L[lay_Kc(p) + a * p + b] = v;
+        }
+      for (int a = 0; a < p; ++a) {
+        L[lay_dLh(p) + a] = 0.5 * dL[a];
+        L[lay_dRh(p) + a] = 0.5 * dR[a];
+      }
+    }
+    // penalty shares and face increments (Eq. (taue), Eq. (tau))
+    const double s = m.penalty * (m.k + 1) * (m.k + 1);
+    const bool per = m.desc.bc_lo[dir] == SIPG_BC_PERIODIC;
+    for (int i = 0; i < n; ++i) tab[(size_t)i * st + lay_ts(p)] = s * tab[(size_t)i * st + lay_t(p)];
+    for (int i = 0; i < n; ++i) {
+      const double ts = tab[(size_t)i * st + lay_ts(p)];
+      const int jl = i > 0 ? i - 1 : (per ? n - 1 : -1);
+      const int jr = i < n - 1 ? i + 1 : (per ? 0 : -1);
+      const double tl = jl >= 0 ? tab[(size_t)jl * st + lay_ts(p)] : ts;
+      const double tr = jr >= 0 ? tab[(size_t)jr * st + lay_ts(p)] : ts;
+      tab[(size_t)i * st + lay_dTL(p)] = tl > ts ? tl - ts : 0.0;
+      tab[(size_t)i * st + lay_dTR(p)] = tr > ts ? tr - ts : 0.0;
     }
   }
-  // upload (double and float copies)
+  // upload (double, float and double-float copies)
   for (int dir = 0; dir < 3; ++dir) {
     if (m.dtab64[dir]) cudaFree(m.dtab64[dir]);
     if (m.dtab32[dir]) cudaFree(m.dtab32[dir]);
+    if (m.dtabdf[dir]) cudaFree(m.dtabdf[dir]);
     m.dtab64[dir] = nullptr;
     m.dtab32[dir] = nullptr;
+    m.dtabdf[dir] = nullptr;
     size_t cnt = m.htab[dir].size();
     cudaError_t e = cudaMalloc(&m.dtab64[dir], cnt * sizeof(double));
     if (e != cudaSuccess) return fail(SIPG_ENOMEM, "cudaMalloc of geometry tables failed");
@@ -260,6 +291,12 @@ int build_tables(Mesh& m) {
     e = cudaMemcpy(m.dtab64[dir], m.htab[dir].data(), cnt * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload geometry tables");
     e = cudaMemcpy(m.dtab32[dir], f.data(), cnt * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload geometry tables");
+    std::vector<dfl> dd(cnt);
+    for (size_t j = 0; j < cnt; ++j) dd[j] = dfl(m.htab[dir][j]);
+    e = cudaMalloc(&m.dtabdf[dir], cnt * sizeof(dfl));
+    if (e != cudaSuccess) return fail(SIPG_ENOMEM, "cudaMalloc of geometry tables failed");
+    e = cudaMemcpy(m.dtabdf[dir], dd.data(), cnt * sizeof(dfl), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload geometry tables");
   }
   return SIPG_OK;

@@ -62,6 +62,42 @@ def test_laplace_f64_parity(name, c, k, pen):
     assert scaled_err(y, y_ref, norm_a, x) <= TOL64
 
 
+@pytest.mark.parametrize("name,c,k,pen", CASES, ids=[x[0] for x in CASES])
+def test_laplace_f64_double_float_parity(name, c, k, pen):
+    """The FP64 operator evaluated in double-float arithmetic (FP32 pairs) meets
+    the same 1e-12 bar as native FP64."""
+    from paper_1607_01323_gb300 import apply_helmholtz_f64, apply_laplace_f64
+    op = SIPG(oracle_spec(c), k, penalty_factor=pen)
+    m = gpu_mesh(c, k, penalty=pen)
+    m.set_f64_arithmetic("double_float")
+    N = m.n_dofs
+    x = uniform(2 * N, "x")
+    A = op.assemble()
+    y_ref = np.concatenate([A @ x[:N], A @ x[N:]])
+    y = apply_laplace_f64(m, _cuda(x)).cpu().numpy()
+    assert scaled_err(y, y_ref, abs(A).sum(axis=1).max(), x) <= TOL64
+    cm, nu = 1500.0, 1.0 / 180.0
+    H = op.assemble(mass_coef=cm, nu=nu)
+    y = apply_helmholtz_f64(m, _cuda(x[:N]), cm, nu).cpu().numpy()
+    assert scaled_err(y, H @ x[:N], abs(H).sum(axis=1).max(), x[:N]) <= TOL64
+
+
+def test_double_float_dynamic_range():
+    """Inputs spanning many orders of magnitude (and exact zeros) keep the
+    1e-12 scaled bar in double-float."""
+    from paper_1607_01323_gb300 import apply_laplace_f64
+    c = channel((3, 4, 2))
+    k = 4
+    op = SIPG(oracle_spec(c), k)
+    m = gpu_mesh(c, k)
+    m.set_f64_arithmetic("double_float")
+    x = uniform(m.n_dofs, "x") * 10.0 ** (8 * uniform(m.n_dofs, "exp"))
+    x[::7] = 0.0
+    A = op.assemble()
+    y = apply_laplace_f64(m, _cuda(x)).cpu().numpy()
+    assert scaled_err(y, A @ x, abs(A).sum(axis=1).max(), x) <= TOL64
+
+
 @pytest.mark.parametrize("cpb", [1, 3, 5, 7])
 def test_laplace_ragged_tiles(cpb):
     """Cells per block that do not divide the cell count leave a ragged last tile."""

@@ -65,6 +65,25 @@ def test_poisson_jacobi_cg_channel(use_graph):
     assert np.linalg.norm(xg - x_orc) <= 1e-6 * np.linalg.norm(x_orc)
 
 
+def test_poisson_double_float_operator():
+    """CG with the double-float FP64 operator reaches 1e-10 and agrees with the
+    native FP64 solve within the residual bound."""
+    from paper_1607_01323_gb300 import cg_solve
+    c = channel((6, 6, 6))
+    k = 4
+    op = SIPG(oracle_spec(c), k)
+    m = gpu_mesh(c, k)
+    b_gpu, b_orc = manufactured_rhs(m, op)
+    xn, rn = cg_solve(m, b_gpu, precond="jacobi", rtol=1e-10)
+    m.set_f64_arithmetic("double_float")
+    xd, rd = cg_solve(m, b_gpu, precond="jacobi", rtol=1e-10)
+    assert rn.converged and rd.converged
+    A = op.assemble()
+    xg = xd.cpu().numpy()
+    assert np.linalg.norm(b_orc - A @ xg) <= 1e-9 * np.linalg.norm(b_orc)
+    assert np.linalg.norm(xg - xn.cpu().numpy()) <= distance_bound(A, b_orc, xg, xn.cpu().numpy())
+
+
 def test_graph_and_loop_bitwise_equal():
     from paper_1607_01323_gb300 import cg_solve
     c = channel((4, 4, 4))
