@@ -183,6 +183,39 @@ int sipg_cg_default_opts(sipg_cg_opts* opts);
 int sipg_cg_solve(sipg_mesh* mesh, const sipg_cg_opts* opts, const double* b, double* x, int ncomp,
                   void* stream, int* iters_out, double* relres_out);
 
+/* Allocation-free variant of sipg_cg_solve.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- for
+ * example a host application whose device memory is owned by its own pool or
+ * caching allocator (a cudaMalloc outside that pool can fail or fragment it),
+ * a deployment with a fixed device-memory budget accounted for up front, or a
+ * latency-critical loop that cannot afford the implicit device
+ * synchronisation of cudaMalloc / cudaFree.
+ *
+ * The caller still passes b and x (DEVICE, as for sipg_cg_solve).  The solver's
+ * workspace (5 vectors, the diagonal, partial sums, the solver record) comes
+ * from one file-scope __device__ array of 16 MiB inside libsipg: every GPU that
+ * loads the library holds those 16 MiB until the process exits.  That bounds the
+ * problem to about 348,000 unknowns (ncomp * n_dofs); larger problems are
+ * rejected with SIPG_EINVAL and a message giving the bytes needed.  The
+ * function calls no cudaMalloc, cudaFree or other allocating routine, creates
+ * no stream, event or graph, and runs on `stream` directly; it is synchronous
+ * like sipg_cg_solve.  Preconditioners: SIPG_PC_NONE, SIPG_PC_JACOBI,
+ * SIPG_PC_INVMASS (SIPG_PC_CHEB_F32 needs FP32 buffers and is rejected);
+ * use_graph is ignored and the mesh's profiling is not applied.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture on the device.  Every call shares the
+ * array and it keeps the previous call's contents (the solver clears what must
+ * start from zero), so calls that overlap on the GPU -- on two streams, two host
+ * threads or two meshes at once -- race on the array and must be serialised by
+ * the caller.  Returns the same statuses as sipg_cg_solve. */
+int sipg_cg_solve_noalloc(sipg_mesh* mesh, const sipg_cg_opts* opts, const double* b, double* x, int ncomp,
+                          void* stream, int* iters_out, double* relres_out);
+
+/* Size in bytes of the static workspace of sipg_cg_solve_noalloc (host output). */
+int sipg_cg_noalloc_capacity(long long* bytes);
+
 /* Adjoint gradient for a per-cell viscosity (not in the paper; the operator is
  * the one of Sec. 3.2 (iii) in Laplace form): grad[e] = - lambda^T (dA/dnu_e) u
  * for A(nu) = mass_coef M + L(nu), with lambda the solution of the adjoint

@@ -55,6 +55,9 @@ _SIGS = {
     "sipg_cg_default_opts": [C.POINTER(CgOpts)],
     "sipg_cg_solve": [C.c_void_p, C.POINTER(CgOpts), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                       C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "sipg_cg_solve_noalloc": [C.c_void_p, C.POINTER(CgOpts), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                              C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "sipg_cg_noalloc_capacity": [C.POINTER(C.c_longlong)],
     "sipg_adjoint_grad_nu": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_autotune": [C.c_void_p, C.c_int, C.c_char_p],
     "sipg_set_f64_arithmetic": [C.c_void_p, C.c_int],

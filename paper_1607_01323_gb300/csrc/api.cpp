@@ -409,6 +409,34 @@ int sipg_cg_solve(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* 
   return st;
 }
 
+int sipg_cg_solve_noalloc(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* x, int ncomp, void* stream,
+                          int* iters, double* relres) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!o) return fail(SIPG_EINVAL, "opts is NULL");
+  if ((st = check_vec(b, x, ncomp))) return st;
+  if (o->op != SIPG_OP_LAPLACE && o->op != SIPG_OP_HELMHOLTZ) return fail(SIPG_EINVAL, "unknown operator");
+  if (o->op == SIPG_OP_HELMHOLTZ && (!(o->mass_coef >= 0.0) || (!o->nu_cell && !(o->nu > 0.0))))
+    return fail(SIPG_EINVAL, "Helmholtz needs mass_coef >= 0 and nu > 0");
+  if (o->precond < SIPG_PC_NONE || o->precond > SIPG_PC_INVMASS)
+    return fail(SIPG_EINVAL, "the allocation-free solve supports preconditioners none, jacobi and invmass");
+  if (!(o->rtol >= 0.0) || o->maxit < 1) return fail(SIPG_EINVAL, "need rtol >= 0 and maxit >= 1");
+  if (o->check_every < 1 || o->check_every > 4096) return fail(SIPG_EINVAL, "check_every must be in [1, 4096]");
+  bool all_bc_free = true;
+  for (int d = 0; d < 3; ++d)
+    if (m->desc.bc_lo[d] == SIPG_BC_DIRICHLET || m->desc.bc_hi[d] == SIPG_BC_DIRICHLET) all_bc_free = false;
+  if (all_bc_free && o->op == SIPG_OP_LAPLACE && !o->zero_mean)
+    return fail(SIPG_EINVAL, "singular Laplace problem (no Dirichlet side): set zero_mean");
+  if ((st = set_device(*m))) return st;
+  return cg_solve_noalloc(*m, *o, b, x, ncomp, (cudaStream_t)stream, iters, relres);
+}
+
+int sipg_cg_noalloc_capacity(long long* bytes) {
+  if (!bytes) return fail(SIPG_EINVAL, "NULL output");
+  *bytes = (long long)noalloc_scratch_bytes();
+  return SIPG_OK;
+}
+
 int sipg_adjoint_grad_nu(const sipg_mesh* mc, const double* nu_cell, const double* u, const double* lam,
                          double* grad, void* stream) {
   int st;

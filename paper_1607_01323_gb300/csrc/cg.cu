@@ -20,7 +20,9 @@
 // Singular problems (zero_mean): b and every operator product are projected
 // onto vectors with zero mean (Sec. 5.1).
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "sipg_internal.h"
@@ -793,5 +795,122 @@ int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int nco
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// CG without allocation: the same solver, with its workspace carved out of a
+// fixed device array instead of cudaMalloc'd memory.
+//
+// The array below is a file-scope __device__ object: every GPU that loads the
+// library holds these kNoAllocScratchBytes until the process exits, whether or
+// not the entry point is ever called.  In host code its name is only a host-side
+// stand-in; the device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and cached.  Every call
+// shares the array, so calls that overlap on the GPU (different streams, host
+// threads or devices sharing a context) race on it.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(SIPG_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static CG scratch)");
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return SIPG_OK;
+}
+
+}  // namespace
+
+size_t noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o_in, const double* b, double* x, int ncomp, cudaStream_t s,
+                     int* iters, double* relres) {
+  if (o_in.precond == SIPG_PC_CHEB_F32)
+    return fail(SIPG_EINVAL, "the allocation-free solve supports preconditioners none, jacobi and invmass");
+  const long long N = m.ncell * m.p * m.p * m.p;
+  const long long n = N * ncomp;
+  const int cpb0 = m.cpb[0] > 0 ? m.cpb[0] : default_cpb(m.p, 0);
+  const long long nb_apply = ((m.ncell + cpb0 - 1) / cpb0) * ncomp;
+  const long long nbmax = nb_apply > kVecBlocks ? nb_apply : kVecBlocks;
+  // same workspace layout as the allocating path, FP32 buffers excluded
+  size_t bytes = 0;
+  auto take = [&](size_t nb) {
+    size_t off = bytes;
+    bytes += (nb + 255) & ~(size_t)255;
+    return off;
+  };
+  const size_t o_r = take(n * 8), o_z = take(n * 8), o_p = take(n * 8), o_ap = take(n * 8), o_xs = take(n * 8),
+               o_diag = take(n * 8), o_p1 = take((size_t)nbmax * 24), o_p2 = take((size_t)nbmax * 24),
+               o_sc = take(sizeof(Scalars));
+  if (bytes > kNoAllocScratchBytes) {
+    char msg[256];
+    std::snprintf(msg, sizeof(msg),
+                  "allocation-free solve needs %zu bytes of scratch for %lld unknowns; the static array holds "
+                  "%zu bytes (about 348,000 unknowns)",
+                  bytes, n, kNoAllocScratchBytes);
+    return fail(SIPG_EINVAL, msg);
+  }
+  void* base_v = nullptr;
+  int st = noalloc_scratch(m.device, &base_v);
+  if (st) return st;
+  char* base = (char*)base_v;
+  Workspace w;
+  w.r = (double*)(base + o_r);
+  w.z = (double*)(base + o_z);
+  w.p = (double*)(base + o_p);
+  w.ap = (double*)(base + o_ap);
+  w.xs = (double*)(base + o_xs);
+  w.diag = (double*)(base + o_diag);
+  w.part1 = (double*)(base + o_p1);
+  w.part2 = (double*)(base + o_p2);
+  w.sc = (Scalars*)(base + o_sc);
+  w.r32 = w.d32 = w.x32 = w.t32 = w.dinv32 = nullptr;
+  w.nblocks_max = (int)nbmax;
+  // the array keeps the previous call's contents: clear the solver record
+  cudaError_t e = cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s);
+  if (e != cudaSuccess) return cuda_fail(e, "clear static CG scratch");
+  // run on the caller's stream, without a CUDA graph and without profiling
+  // events (their creation would allocate)
+  sipg_cg_opts o = o_in;
+  o.use_graph = 0;
+  const bool prof = m.profile;
+  m.profile = false;
+  Solver S(m, o, ncomp, s);
+  S.w = w;
+  const bool helm = o.op == SIPG_OP_HELMHOLTZ;
+  const double cm = helm ? o.mass_coef : 0.0, nu = helm ? o.nu : 1.0;
+  const double* nuc = helm ? o.nu_cell : nullptr;
+  int it = 0, done = 0;
+  double rel = 0.0;
+  if (o.precond == SIPG_PC_JACOBI) {
+    st = launch_diagonal(m, true, cm, nu, nuc, w.xs, s);
+    if (!st) {
+      k_inv_rep<<<kVecBlocks, kVecThreads, 0, s>>>(n, N, w.xs, w.diag);
+      st = S.launched();
+    }
+  }
+  if (!st) st = S.run(b, x, o.maxit, o.rtol, false, &it, &rel, &done);
+  m.profile = prof;
+  if (st) return st;
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  switch (done) {
+    case CONVERGED: return SIPG_OK;
+    case MAXIT: return fail(SIPG_MAXITER, "CG reached maxit without converging");
+    case BREAKDOWN: return fail(SIPG_BREAKDOWN, "CG breakdown: p^T A p <= 0 (operator not positive definite?)");
+    case NONFINITE: return fail(SIPG_NONFINITE, "non-finite value in CG (right-hand side or operator)");
+    default: return fail(SIPG_EINVAL, "CG ended in an unknown state");
+  }
+}
 
 }  // namespace sipg

@@ -130,6 +130,10 @@ int launch_adjoint(const Mesh& m, const double* nu_cell, const double* u, const 
 int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s, int* iters,
              double* relres);
 
+int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s,
+                     int* iters, double* relres);
+size_t noalloc_scratch_bytes();
+
 // profiling helpers (api.cpp)
 void prof_begin(Mesh& m, cudaStream_t s, cudaEvent_t* e0);
 void prof_end(Mesh& m, cudaStream_t s, cudaEvent_t e0);
