@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(kMaxCellThreads) adjoint_kernel(Geo<double> g,
                        0.0, 0.0, 0.0);
     load_line<double, P>(v1, w1, start, step);
     load_line<double, P>(v2, w2, start, step);
-    matvec<double, P>(a1, L + O::M, v1);
-    matvec<double, P>(a2, L + O::M, v2);
+    matvec(a1, L + O::M, v1);
+    matvec(a2, L + O::M, v2);
     store_line<double, P>(us, w, start, step);
     store_line<double, P>(w1, a1, start, step);
     store_line<double, P>(w2, a2, start, step);
@@ -175,9 +175,9 @@ __global__ void __launch_bounds__(kMaxCellThreads) adjoint_kernel(Geo<double> g,
     const double* My = g.tab[1] + id[1] * O::stride + O::M;
     double v[P], r1[P], r2[P], a2[P];
     load_line<double, P>(v, w1, start, step);
-    matvec<double, P>(r1, My, v);
+    matvec(r1, My, v);
     load_line<double, P>(v, us, start, step);
-    matvec<double, P>(r2, My, v);
+    matvec(r2, My, v);
     load_line<double, P>(a2, w2, start, step);
 #pragma unroll
     for (int a = 0; a < P; ++a) r2[a] += a2[a];
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) adjoint_kernel(Geo<double> g,
     const double* Mx = g.tab[0] + id[0] * O::stride + O::M;
     double v[P], out[P], r1[P], ll[P];
     load_line<double, P>(v, w2, start, step);
-    matvec<double, P>(out, Mx, v);
+    matvec(out, Mx, v);
     load_line<double, P>(r1, w1, start, step);
     load_line_global<double, P>(ll, lc, start, step);
 #pragma unroll

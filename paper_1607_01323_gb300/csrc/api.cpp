@@ -66,16 +66,19 @@ template Geo<double> make_geo<double>(const Mesh&);
 template Geo<float> make_geo<float>(const Mesh&);
 template Geo<dfl> make_geo<dfl>(const Mesh&);
 
+// Default cells per block: the largest count whose p^2 threads per cell fill a
+// 256-thread block with the fewest idle lanes (blocks are rounded up to whole
+// warps): 64, 28, 16, 10, 7, 5, 4 cells for p = 2..8.
 int default_cpb(int p, int precision) {
   (void)precision;
   switch (p) {
-    case 2: return 32;
-    case 3: return 16;
-    case 4: return 8;
-    case 5: return 8;
-    case 6: return 4;
-    case 7: return 4;
-    default: return 2;
+    case 2: return 64;
+    case 3: return 28;
+    case 4: return 16;
+    case 5: return 10;
+    case 6: return 7;
+    case 7: return 5;
+    default: return 4;
   }
 }
 
@@ -517,7 +520,10 @@ int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
   int best = 0;
   float best_ms = 1e30f;
   const int old = m->cpb[precision];
-  for (int c = 1; c <= 64; c *= 2) {
+  for (int c = 1; c <= 64; ++c) {
+    // every feasible count whose block wastes at most 1/8 of its lanes
+    const int thr = c * m->p * m->p, rounded = (thr + 31) / 32 * 32;
+    if (8 * (rounded - thr) > rounded) continue;
     if (sipg_set_cells_per_block(m, precision, c) != SIPG_OK) continue;
     float tot = 0.f;
     bool ok = true;

@@ -26,6 +26,8 @@
 // its own outputs, so there are no atomics and the result is deterministic.
 #pragma once
 
+#include <type_traits>
+
 #include "dfloat.cuh"
 #include "sipg_internal.h"
 
@@ -161,7 +163,7 @@ __device__ __forceinline__ void line_op(T (&w)[P], const T (&u)[P], const T* __r
   }
 }
 
-// y[a] = sum_b A[a][b] v[b] (+ y[a] when acc)
+// y[a] = sum_b A[a][b] v[b]
 template <typename T, int P>
 __device__ __forceinline__ void matvec(T (&out)[P], const T* __restrict__ A, const T (&v)[P]) {
 #pragma unroll
@@ -171,6 +173,26 @@ __device__ __forceinline__ void matvec(T (&out)[P], const T* __restrict__ A, con
     for (int b = 0; b < P; ++b) s = fma(A[a * P + b], v[b], s);
     out[a] = s;
   }
+}
+
+// sum_b a[b] v[b]
+template <typename T, int P>
+__device__ __forceinline__ T dotp(const T* __restrict__ a, const T (&v)[P]) {
+  T s = T(0);
+#pragma unroll
+  for (int b = 0; b < P; ++b) s = fma(a[b], v[b], s);
+  return s;
+}
+template <int P>
+__device__ __forceinline__ dfl dotp(const dfl* __restrict__ a, const dfl (&v)[P]) {
+  return df_dot<P>(a, v);
+}
+
+// double-float contraction: one lazily renormalised dot product per output
+template <int P>
+__device__ __forceinline__ void matvec(dfl (&out)[P], const dfl* __restrict__ A, const dfl (&v)[P]) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) out[a] = df_dot<P>(A + a * P, v);
 }
 
 // Index of element (a, b, c) inside one cell.
@@ -367,8 +389,8 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
                   c.LR, c.nuR, c.tauFR, tau_e);
     load_line<T, P>(v1, w1, start, step);
     load_line<T, P>(v2, w2, start, step);
-    matvec<T, P>(a1, c.L + LayerOff<P>::M, v1);
-    matvec<T, P>(a2, c.L + LayerOff<P>::M, v2);
+    matvec(a1, c.L + LayerOff<P>::M, v1);
+    matvec(a2, c.L + LayerOff<P>::M, v2);
     store_line<T, P>(us, w, start, step);
     store_line<T, P>(w1, a1, start, step);
     store_line<T, P>(w2, a2, start, step);
@@ -380,9 +402,9 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
     const T* My = g.tab[1] + id[1] * LayerOff<P>::stride + LayerOff<P>::M;
     T v[P], r1[P], r2[P], a2[P];
     load_line<T, P>(v, w1, start, step);
-    matvec<T, P>(r1, My, v);
+    matvec(r1, My, v);
     load_line<T, P>(v, us, start, step);
-    matvec<T, P>(r2, My, v);
+    matvec(r2, My, v);
     load_line<T, P>(a2, w2, start, step);
 #pragma unroll
     for (int a = 0; a < P; ++a) r2[a] += a2[a];
@@ -397,7 +419,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
     const T* Mx = g.tab[0] + id[0] * LayerOff<P>::stride + LayerOff<P>::M;
     T v[P], out[P], r1[P];
     load_line<T, P>(v, w2, start, step);
-    matvec<T, P>(out, Mx, v);
+    matvec(out, Mx, v);
     load_line<T, P>(r1, w1, start, step);
     T* yo = y + cbase + (long long)e * P3 + start;
 #pragma unroll
@@ -427,11 +449,9 @@ __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* _
                                           const T (&uL)[P], const T* __restrict__ LL, T tauFL, int kindR,
                                           const T (&uR)[P], const T* __restrict__ LR, T tauFR, T tau2e) {
   using O = LayerOff<P>;
-  matvec<T, P>(w, L + O::Kc, u);
+  matvec(w, L + O::Kc, u);
   if (kindR == 0) {
-    T gn = T(0);
-#pragma unroll
-    for (int a = 0; a < P; ++a) gn = fma(LR[O::dLh + a], uR[a], gn);
+    const T gn = dotp(LR + O::dLh, uR);
     const T J = u[P - 1] - uR[0];
     w[P - 1] += fma(tauFR, J, -gn);
     const T ur = uR[0];
@@ -441,9 +461,7 @@ __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* _
     w[P - 1] = fma(tau2e, u[P - 1], w[P - 1]);
   }
   if (kindL == 0) {
-    T gn = T(0);
-#pragma unroll
-    for (int a = 0; a < P; ++a) gn = fma(LL[O::dRh + a], uL[a], gn);
+    const T gn = dotp(LL + O::dRh, uL);
     const T J = uL[P - 1] - u[0];
     w[0] += fma(-tauFL, J, gn);
     const T ul = -uL[P - 1];
@@ -463,8 +481,18 @@ __device__ __forceinline__ void load_line_global_cvt(T (&v)[P], const S* __restr
   for (int a = 0; a < P; ++a) v[a] = cvt_in<T, S>(__ldg(base + start + a * step));
 }
 
+// Blocks per SM requested from the register allocator: the double-float
+// kernel fits 80 registers without spills up to p = 5, which allows three
+// 256-thread blocks (24 warps) per SM; the FP32 kernel fits 64 registers (four
+// blocks) up to p = 6; native FP64 is FP64-issue-bound and keeps the default.
+template <typename T, int P>
+struct UniformMinBlocks {
+  static constexpr int value = std::is_same<T, dfl>::value ? (P <= 5 ? 3 : 1)
+                               : (std::is_same<T, float>::value ? (P <= 6 ? 4 : (P == 7 ? 3 : 2)) : 1);
+};
+
 template <typename T, typename S, int P>
-__global__ void __launch_bounds__(kMaxCellThreads) apply_uniform_kernel(Geo<T> g, const S* __restrict__ x,
+__global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value) apply_uniform_kernel(Geo<T> g, const S* __restrict__ x,
                                                                         S* __restrict__ y, int cpb, T mass_rel,
                                                                         T scale, int do_scale, int do_mass,
                                                                         double* __restrict__ dots) {
@@ -501,7 +529,6 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_uniform_kernel(Geo<T> g
             g.tab[2][id[2] * O::stride + O::ts];
   }
   const T tau2e = tau_e + tau_e;
-  T ux[P];
   if (active) {
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
@@ -513,10 +540,6 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_uniform_kernel(Geo<T> g
       face_neighbor(g, dir, 1, id[dir], e, nbR, kR, jr);
       T u[P], uL[P], uR[P], w[P];
       load_line<T, P>(u, us, start, step);
-      if (dir == 0) {
-#pragma unroll
-        for (int a = 0; a < P; ++a) ux[a] = u[a];
-      }
       if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step);
       if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step);
       line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
@@ -529,10 +552,21 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_uniform_kernel(Geo<T> g
     int start, step;
     line_geom<P>(2, ti, tj, start, step);
     const T* L = g.tab[2] + id[2] * O::stride;
+    // each contraction is finished and stored before the next starts (short
+    // live ranges, fewer registers); every thread touches only its own z-line
+    {
+      T v[P], r[P];
+      load_line<T, P>(v, w1, start, step);
+      matvec(r, L + O::M, v);
+      store_line<T, P>(w1, r, start, step);
+      load_line<T, P>(v, w2, start, step);
+      matvec(r, L + O::M, v);
+      store_line<T, P>(w2, r, start, step);
+    }
     int nbL, nbR, kL, kR, jl, jr;
     face_neighbor(g, 2, 0, id[2], e, nbL, kL, jl);
     face_neighbor(g, 2, 1, id[2], e, nbR, kR, jr);
-    T u[P], uL[P], uR[P], w[P], v1[P], v2[P], a1[P], a2[P];
+    T u[P], uL[P], uR[P], w[P];
     load_line<T, P>(u, us, start, step);
     if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step);
     if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step);
@@ -540,33 +574,27 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_uniform_kernel(Geo<T> g
                     kR == 0 ? g.tab[2] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
     if (do_mass) {
       T mu[P];
-      matvec<T, P>(mu, L + O::M, u);
+      matvec(mu, L + O::M, u);
 #pragma unroll
       for (int a = 0; a < P; ++a) w[a] = fma(mass_rel, mu[a], w[a]);
     }
-    load_line<T, P>(v1, w1, start, step);
-    load_line<T, P>(v2, w2, start, step);
-    matvec<T, P>(a1, L + O::M, v1);
-    matvec<T, P>(a2, L + O::M, v2);
     store_line<T, P>(us, w, start, step);
-    store_line<T, P>(w1, a1, start, step);
-    store_line<T, P>(w2, a2, start, step);
   }
   __syncthreads();
   if (active) {
     int start, step;
     line_geom<P>(1, ti, tj, start, step);
     const T* My = g.tab[1] + id[1] * O::stride + O::M;
-    T v[P], r1[P], r2[P], a2[P];
+    T v[P], r[P];
     load_line<T, P>(v, w1, start, step);
-    matvec<T, P>(r1, My, v);
+    matvec(r, My, v);
+    store_line<T, P>(w1, r, start, step);
     load_line<T, P>(v, us, start, step);
-    matvec<T, P>(r2, My, v);
-    load_line<T, P>(a2, w2, start, step);
+    matvec(r, My, v);
+    load_line<T, P>(v, w2, start, step);
 #pragma unroll
-    for (int a = 0; a < P; ++a) r2[a] += a2[a];
-    store_line<T, P>(w1, r1, start, step);
-    store_line<T, P>(w2, r2, start, step);
+    for (int a = 0; a < P; ++a) r[a] += v[a];
+    store_line<T, P>(w2, r, start, step);
   }
   __syncthreads();
   double d_xy = 0.0, d_y = 0.0, d_x = 0.0;
@@ -576,7 +604,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_uniform_kernel(Geo<T> g
     const T* Mx = g.tab[0] + id[0] * O::stride + O::M;
     T v[P], out[P], r1[P];
     load_line<T, P>(v, w2, start, step);
-    matvec<T, P>(out, Mx, v);
+    matvec(out, Mx, v);
     load_line<T, P>(r1, w1, start, step);
     S* yo = y + cbase + (long long)e * P3 + start;
 #pragma unroll
@@ -586,7 +614,10 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_uniform_kernel(Geo<T> g
       yo[a] = cvt_out<S, T>(out[a]);
     }
     if (dots) {
-      // line sums in the compute type, one conversion per line
+      // line sums in the compute type, one conversion per line; the x-line of
+      // the input is read again (cached) instead of being held in registers
+      T ux[P];
+      load_line_global_cvt<T, S, P>(ux, xc + (long long)e * P3, start, step);
       T sxy(0), sy(0), sx(0);
 #pragma unroll
       for (int a = 0; a < P; ++a) {
@@ -637,7 +668,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<doubl
       line_geom<P>(dir, ti, tj, start, step);
       double v[P], o[P];
       load_line<double, P>(v, us, start, step);
-      matvec<double, P>(o, g.tab[dir] + id[dir] * O::stride + O::Mi, v);
+      matvec(o, g.tab[dir] + id[dir] * O::stride + O::Mi, v);
       store_line<double, P>(us, o, start, step);
     }
     __syncthreads();
@@ -648,7 +679,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<doubl
     line_geom<P>(0, ti, tj, start, step);
     double v[P], o[P];
     load_line<double, P>(v, us, start, step);
-    matvec<double, P>(o, g.tab[0] + id[0] * O::stride + O::Mi, v);
+    matvec(o, g.tab[0] + id[0] * O::stride + O::Mi, v);
     const long long off = cbase + (long long)e * P3 + start;
     for (int a = 0; a < P; ++a) y[off + a] = o[a];
     if (dots) {

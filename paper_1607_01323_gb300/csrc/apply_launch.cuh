@@ -19,7 +19,7 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
   const size_t smem = (size_t)3 * cpb * P * P * P * sizeof(T);
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
   const bool uniform = stiff && nu_cell == nullptr;
-  if (smem > 48 * 1024) {
+  if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
     cudaError_t e = uniform ? cudaFuncSetAttribute(apply_uniform_kernel<T, T, P>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                             : cudaFuncSetAttribute(apply_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -32,7 +32,7 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
     if constexpr (std::is_same<T, double>::value) {
       if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
         const Geo<dfl> gd = make_geo<dfl>(m);
-        if (smem > 48 * 1024) {
+        if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
           cudaError_t e = cudaFuncSetAttribute(apply_uniform_kernel<dfl, double, P>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");

@@ -13,7 +13,7 @@ int launch_inverse_mass_p(const Mesh& m, const double* x, double* y, int ncomp, 
   const size_t smem = (size_t)cpb * P * P * P * sizeof(double);
   const int threads = (cpb * P * P + 31) / 32 * 32;  // whole warps
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
-  if (smem > 48 * 1024) {
+  if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
     cudaError_t e = cudaFuncSetAttribute(inverse_mass_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(inverse mass)");
   }
@@ -69,7 +69,7 @@ int launch_adjoint_p(const Mesh& m, const double* nu_cell, const double* u, cons
   const int threads = (cpb * P * P + 31) / 32 * 32;
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
   const size_t smem = sizeof(double) * ((size_t)3 * cpb * P * P * P + (size_t)8 * cpb * P * P + threads);
-  if (smem > 48 * 1024) {
+  if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
     cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(adjoint)");
   }
