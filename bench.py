@@ -426,6 +426,7 @@ def _timed(fn, reps=3):
 
 def run_config(args):
     """Timings of the other workload configurations (one JSON line each):
+    c1: the 4^3 periodic unit cube at k=3 (operator apply only);
     c3: 3-component viscous Helmholtz on the 64^3 k=3 channel (apply, autotune,
         graph-captured CG with M^-1 and Jacobi);
     c4: Neumann-channel Poisson 48^3 k=5, FP32 Chebyshev(4) + FP64 flexible CG
@@ -439,7 +440,13 @@ def run_config(args):
                                         apply_mass_f64, autotune, cg_solve, inputs)
     w = WORKLOAD
     out = {"workload": args.workload, "f64_arithmetic": args.f64}
-    if args.workload == "c3":
+    if args.workload == "c1":
+        m = Mesh((4, 4, 4), k=3)  # periodic unit cube, affine, tau = 192
+        m.set_f64_arithmetic(args.f64)
+        x = torch.tensor(inputs.uniform(0, "x", m.n_dofs), device="cuda")
+        y = torch.empty_like(x)
+        t, _ = _timed(lambda: [apply_laplace_f64(m, x, y) for _ in range(100)], reps=5)
+        out["apply_f64"] = {"us": 1e6 * t / 100, "dofs": m.n_dofs, "note": "launch-latency bound (64 cells)"}
         m = Mesh((64, 64, 64), w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping="channel", gamma=1.8, k=3)
         m.set_f64_arithmetic(args.f64)
         N = m.n_dofs
@@ -533,7 +540,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--f64", default="double_float", choices=["native", "double_float"],
                     help="arithmetic of the FP64 operator (double_float: FP32 pairs on the FP32 pipes)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
                     help="c2 (default) is the bench step; c3-c5 print timings of the other configurations")
     args = ap.parse_args()
     if args.mode == "apply":

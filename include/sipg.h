@@ -238,8 +238,9 @@ int sipg_autotune(sipg_mesh* mesh, int precision, const char* cache_path);
  * sum-factorised operator in double-float arithmetic (pairs of FP32 with exact
  * product errors and TwoSum, about 2^-46 relative per operation) on the FP32
  * pipes, which issue 64 times the FP64 rate on GB300; results stay within the
- * FP64 parity tolerance (1e-12 of ||A|| ||x||).  The per-cell-viscosity
- * operator, the mass, inverse-mass and adjoint kernels always use FP64. */
+ * FP64 parity tolerance (1e-12 of ||A|| ||x||).  The same choice applies to
+ * sipg_apply_inverse_mass_f64 (and the inverse-mass preconditioner).  The
+ * per-cell-viscosity operator, the mass and adjoint kernels always use FP64. */
 int sipg_set_f64_arithmetic(sipg_mesh* mesh, int mode);
 int sipg_get_f64_arithmetic(const sipg_mesh* mesh, int* mode);
 

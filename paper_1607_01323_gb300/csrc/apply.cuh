@@ -239,6 +239,7 @@ __device__ __forceinline__ void store_line(T* base, const T (&v)[P], int start, 
 // Block reduction of three doubles; thread 0 writes out[0..2].
 __device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out) {
   __shared__ double red[3][32];
+  __syncthreads();  // a previous call may still read red
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
@@ -268,6 +269,38 @@ __device__ __forceinline__ void block_reduce3(double a, double b, double c, doub
       out[1] = b;
       out[2] = c;
     }
+  }
+}
+
+// Partial sums of one block to the sink; the last block of the grid adds all
+// partials (fixed order, deterministic) into sink.totals.  Called by every
+// thread of the block.
+__device__ __forceinline__ void sink_dots(const DotSink& s, double a, double b, double c) {
+  const unsigned nb = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  block_reduce3(a, b, c, s.partials + 3 * (long long)bid);
+  if (!s.counter) return;
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partial is visible before the count
+    last = atomicAdd(s.counter, 1u) == nb - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double x = 0.0, y = 0.0, z = 0.0;
+  for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
+    x += __ldcg(s.partials + 3 * i);
+    y += __ldcg(s.partials + 3 * i + 1);
+    z += __ldcg(s.partials + 3 * i + 2);
+  }
+  double t[3];
+  block_reduce3(x, y, z, t);  // thread 0 holds the totals
+  if (threadIdx.x == 0) {
+    s.totals[0] = t[0];
+    s.totals[1] = t[1];
+    s.totals[2] = t[2];
+    *s.counter = 0u;
   }
 }
 
@@ -314,7 +347,9 @@ __device__ __forceinline__ DirCtx<T, P> dir_ctx(const Geo<T>& g, int dir, const 
 template <typename T, int P>
 __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const T* __restrict__ x, T* __restrict__ y, int cpb,
                                                      T mass_coef, T nu, const T* __restrict__ nu_cell, int stiffness,
-                                                     double* __restrict__ dots) {
+                                                     DotSink sink) {
+  if (sink.skip && *sink.skip) return;
+  double* dots = sink.partials;
   constexpr int P2 = P * P, P3 = P * P * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);
@@ -436,7 +471,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
       }
     }
   }
-  if (dots) block_reduce3(d_xy, d_y, d_x, dots + 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
+  if (dots) sink_dots(sink, d_xy, d_y, d_x);
 }
 
 // Uniform-viscosity line operator (unit viscosity; the caller scales): the own
@@ -495,7 +530,9 @@ template <typename T, typename S, int P>
 __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value) apply_uniform_kernel(Geo<T> g, const S* __restrict__ x,
                                                                         S* __restrict__ y, int cpb, T mass_rel,
                                                                         T scale, int do_scale, int do_mass,
-                                                                        double* __restrict__ dots) {
+                                                                        DotSink sink) {
+  if (sink.skip && *sink.skip) return;
+  double* dots = sink.partials;
   using O = LayerOff<P>;
   constexpr int P2 = P * P, P3 = P * P * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -510,8 +547,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   const bool active = cs < cpb && e < g.ncell;  // blocks are rounded up to whole warps
   const long long cbase = (long long)blockIdx.y * g.ncell * P3;
   const S* __restrict__ xc = x + cbase;
+  const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);  // cells staged in this block
   {
-    const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
     const S* xb = xc + cell0 * P3;
     for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx]);
   }
@@ -540,8 +577,22 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
       face_neighbor(g, dir, 1, id[dir], e, nbR, kR, jr);
       T u[P], uL[P], uR[P], w[P];
       load_line<T, P>(u, us, start, step);
-      if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step);
-      if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step);
+      // a neighbour staged in this block is read from shared memory (read-only
+      // during phases X and Y), otherwise from global memory
+      if (kL == 0) {
+        const long long sl = (long long)nbL - cell0;
+        if (sl >= 0 && sl < nc)
+          load_line<T, P>(uL, su + sl * P3, start, step);
+        else
+          load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step);
+      }
+      if (kR == 0) {
+        const long long sr = (long long)nbR - cell0;
+        if (sr >= 0 && sr < nc)
+          load_line<T, P>(uR, su + sr * P3, start, step);
+        else
+          load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step);
+      }
       line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
                       kR == 0 ? g.tab[dir] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
       store_line<T, P>(dir == 0 ? w1 : w2, w, start, step);
@@ -630,17 +681,20 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
       d_x = cvt_out<double, T>(sx);
     }
   }
-  if (dots) block_reduce3(d_xy, d_y, d_x, dots + 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));
+  if (dots) sink_dots(sink, d_xy, d_y, d_x);
 }
 
 // y = M^-1 x = (Mx^-1 x My^-1 x Mz^-1) x cell by cell (Sec. 5: tensorial inverse
-// mass with square 1D transforms).  Optional dots as in apply_kernel (x.y).
-template <int P>
-__global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<double> g, const double* __restrict__ x,
-                                                            double* __restrict__ y, int cpb, double* __restrict__ dots) {
+// mass with square 1D transforms).  T is the arithmetic (double or
+// double-float), S the storage type.  Optional per-block partials (x.y, sum y,
+// sum x) for the CG.
+template <typename T, typename S, int P>
+__global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<T> g, const S* __restrict__ x,
+                                                                       S* __restrict__ y, int cpb,
+                                                                       double* __restrict__ dots) {
   constexpr int P2 = P * P, P3 = P * P * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* su = reinterpret_cast<double*>(smem_raw);
+  T* su = reinterpret_cast<T*>(smem_raw);
   const int cs = threadIdx.x / P2;
   const int t = threadIdx.x - cs * P2;
   const int ti = t % P, tj = t / P;
@@ -650,11 +704,11 @@ __global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<doubl
   const long long cbase = (long long)blockIdx.y * g.ncell * P3;
   {
     const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
-    const double* xb = x + cbase + cell0 * P3;
-    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = xb[idx];
+    const S* xb = x + cbase + cell0 * P3;
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx]);
   }
   __syncthreads();
-  double* us = su + cs * P3;
+  T* us = su + cs * P3;
   int id[3] = {0, 0, 0};
   if (active) {
     id[0] = e % g.n[0];
@@ -666,10 +720,10 @@ __global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<doubl
     if (active) {
       int start, step;
       line_geom<P>(dir, ti, tj, start, step);
-      double v[P], o[P];
-      load_line<double, P>(v, us, start, step);
+      T v[P], o[P];
+      load_line<T, P>(v, us, start, step);
       matvec(o, g.tab[dir] + id[dir] * O::stride + O::Mi, v);
-      store_line<double, P>(us, o, start, step);
+      store_line<T, P>(us, o, start, step);
     }
     __syncthreads();
   }
@@ -677,18 +731,23 @@ __global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<doubl
   if (active) {
     int start, step;
     line_geom<P>(0, ti, tj, start, step);
-    double v[P], o[P];
-    load_line<double, P>(v, us, start, step);
+    T v[P], o[P];
+    load_line<T, P>(v, us, start, step);
     matvec(o, g.tab[0] + id[0] * O::stride + O::Mi, v);
     const long long off = cbase + (long long)e * P3 + start;
-    for (int a = 0; a < P; ++a) y[off + a] = o[a];
+    for (int a = 0; a < P; ++a) y[off + a] = cvt_out<S, T>(o[a]);
     if (dots) {
+      T xv[P];
+      load_line_global_cvt<T, S, P>(xv, x + cbase + (long long)e * P3, start, step);
+      T sxy(0), sy(0), sx(0);
       for (int a = 0; a < P; ++a) {
-        const double xv = x[off + a];
-        d_xy += o[a] * xv;
-        d_y += o[a];
-        d_x += xv;
+        sxy = fma(o[a], xv[a], sxy);
+        sy += o[a];
+        sx += xv[a];
       }
+      d_xy = cvt_out<double, T>(sxy);
+      d_y = cvt_out<double, T>(sy);
+      d_x = cvt_out<double, T>(sx);
     }
   }
   if (dots) block_reduce3(d_xy, d_y, d_x, dots + 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));

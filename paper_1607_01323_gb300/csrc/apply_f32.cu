@@ -6,8 +6,8 @@ namespace sipg {
 
 template <>
 int launch_apply<float>(const Mesh& m, const float* x, float* y, int ncomp, float cm, float nu, const float* nu_cell,
-                        bool stiff, double* dots, int* nblocks, cudaStream_t s) {
-  return launch_apply_dispatch<float>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+                        bool stiff, const DotSink* sink, int* nblocks, cudaStream_t s) {
+  return launch_apply_dispatch<float>(m, x, y, ncomp, cm, nu, nu_cell, stiff, sink, nblocks, s);
 }
 
 }  // namespace sipg

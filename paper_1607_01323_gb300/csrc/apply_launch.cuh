@@ -10,7 +10,7 @@ namespace sipg {
 
 template <typename T, int P>
 static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu, const T* nu_cell, bool stiff,
-                          double* dots, int* nblocks, cudaStream_t s) {
+                          const DotSink* sink, int* nblocks, cudaStream_t s) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
   const int cpb = m.cpb[prec] > 0 ? m.cpb[prec] : default_cpb(P, prec);
   const Geo<T> g = make_geo<T>(m);
@@ -19,6 +19,7 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
   const size_t smem = (size_t)3 * cpb * P * P * P * sizeof(T);
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
   const bool uniform = stiff && nu_cell == nullptr;
+  const DotSink ds = sink ? *sink : DotSink();
   if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
     cudaError_t e = uniform ? cudaFuncSetAttribute(apply_uniform_kernel<T, T, P>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
@@ -38,16 +39,16 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
           if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
         }
         apply_uniform_kernel<dfl, double, P><<<grid, threads, smem, s>>>(gd, x, y, cpb, dfl(cm / nu), dfl(nu),
-                                                                         do_scale, do_mass, dots);
+                                                                         do_scale, do_mass, ds);
         if (nblocks) *nblocks = (int)(grid.x * grid.y);
         const_cast<Mesh&>(m).launches++;
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch");
       }
     }
-    apply_uniform_kernel<T, T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm / nu, nu, do_scale, do_mass, dots);
+    apply_uniform_kernel<T, T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm / nu, nu, do_scale, do_mass, ds);
   } else {
-    apply_kernel<T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm, nu, nu_cell, stiff ? 1 : 0, dots);
+    apply_kernel<T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm, nu, nu_cell, stiff ? 1 : 0, ds);
   }
   if (nblocks) *nblocks = (int)(grid.x * grid.y);
   const_cast<Mesh&>(m).launches++;
@@ -57,15 +58,15 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
 
 template <typename T>
 static int launch_apply_dispatch(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu, const T* nu_cell, bool stiff,
-                                 double* dots, int* nblocks, cudaStream_t s) {
+                                 const DotSink* sink, int* nblocks, cudaStream_t s) {
   switch (m.p) {
-    case 2: return launch_apply_p<T, 2>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
-    case 3: return launch_apply_p<T, 3>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
-    case 4: return launch_apply_p<T, 4>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
-    case 5: return launch_apply_p<T, 5>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
-    case 6: return launch_apply_p<T, 6>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
-    case 7: return launch_apply_p<T, 7>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
-    case 8: return launch_apply_p<T, 8>(m, x, y, ncomp, cm, nu, nu_cell, stiff, dots, nblocks, s);
+    case 2: return launch_apply_p<T, 2>(m, x, y, ncomp, cm, nu, nu_cell, stiff, sink, nblocks, s);
+    case 3: return launch_apply_p<T, 3>(m, x, y, ncomp, cm, nu, nu_cell, stiff, sink, nblocks, s);
+    case 4: return launch_apply_p<T, 4>(m, x, y, ncomp, cm, nu, nu_cell, stiff, sink, nblocks, s);
+    case 5: return launch_apply_p<T, 5>(m, x, y, ncomp, cm, nu, nu_cell, stiff, sink, nblocks, s);
+    case 6: return launch_apply_p<T, 6>(m, x, y, ncomp, cm, nu, nu_cell, stiff, sink, nblocks, s);
+    case 7: return launch_apply_p<T, 7>(m, x, y, ncomp, cm, nu, nu_cell, stiff, sink, nblocks, s);
+    case 8: return launch_apply_p<T, 8>(m, x, y, ncomp, cm, nu, nu_cell, stiff, sink, nblocks, s);
     default: return fail(SIPG_EINVAL, "unsupported degree");
   }
 }

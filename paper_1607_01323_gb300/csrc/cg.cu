@@ -45,6 +45,9 @@ struct Scalars {
   double tol2;    // rtol^2
   double ntot;    // number of unknowns (for the mean)
   int done, iters, maxit, record;
+  double tot[3];                  // totals of the operator's dots (p.Ap, sum Ap, sum p)
+  double tot_update[3];           // totals of the update's dots (r.r, r.z, z.q)
+  unsigned cnt_apply, cnt_update;  // last-block counters
   double lan_alpha[kMaxLanczos];
   double lan_beta[kMaxLanczos];
 };
@@ -114,6 +117,47 @@ __device__ void block_partial3(double a, double b, double c, double* out) {
   }
 }
 
+// FP32 value of the top 24 mantissa bits of a double (truncation, by bit
+// manipulation: no FP64 instruction); 0 below the normal FP32 range, +inf above
+// it and for inf / NaN (so a non-finite residual still stops the solver).
+__device__ __forceinline__ float f64_top24(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int fe = (int)((u >> 52) & 0x7ff) - 1023 + 127;
+  if (fe < 1) return 0.f;
+  if (fe > 254) return __int_as_float(0x7f800000);
+  const unsigned bits = ((unsigned)(u >> 32) & 0x80000000u) | ((unsigned)fe << 23) | ((unsigned)(u >> 29) & 0x7fffffu);
+  return __int_as_float((int)bits);
+}
+
+// Block-wide sums of three values; thread 0 writes out[0..2].
+__device__ void block_total3(double a, double b, double c, double* out) {
+  __shared__ double sh[3][32];
+  __syncthreads();  // a previous reduction may still read sh
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][wid] = a;
+    sh[1][wid] = b;
+    sh[2][wid] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      s0 += sh[0][w];
+      s1 += sh[1][w];
+      s2 += sh[2][w];
+    }
+    out[0] = s0;
+    out[1] = s1;
+    out[2] = s2;
+  }
+}
+
 // ---------------------------------------------------------------- init
 // r = b - Ax; partials (sum r, sum b, b.b)
 __global__ void k_init_residual(long long n, const double* __restrict__ b, const double* __restrict__ ax,
@@ -144,6 +188,7 @@ __global__ void k_init_scalars(Scalars* sc, const double* __restrict__ part, int
     sc->done = RUNNING;
     sc->record = record;
     sc->alpha = sc->beta = 0.0;
+    sc->cnt_apply = sc->cnt_update = 0u;
     if (!finite(sc->bb)) sc->done = NONFINITE;
   }
 }
@@ -165,55 +210,127 @@ __global__ void k_init_precond(const Scalars* __restrict__ sc, long long n, doub
 }
 
 // ---------------------------------------------------------------- iteration
-// alpha = r.z / (p.Ap - mean sum p); mean = sum(Ap)/N when zero_mean
-__global__ void k_alpha(Scalars* sc, const double* __restrict__ part, int nb, int zero_mean) {
-  if (sc->done) return;
-  __shared__ double s[3];
-  block_sum3(part, nb, s);
-  if (threadIdx.x == 0) {
-    const double mean = zero_mean ? s[1] / sc->ntot : 0.0;
-    const double pap = s[0] - mean * s[2];
-    sc->mean = mean;
-    if (!finite(pap)) {
-      sc->done = NONFINITE;
-    } else if (!(pap > 0.0)) {
-      sc->done = BREAKDOWN;
-    } else {
-      sc->alpha = sc->rz / pap;
-    }
-  }
-}
-
-// x += alpha p; r -= alpha (Ap - mean); Jacobi/none: z = D^-1 r (diag holds
-// the inverse diagonal).  partials: (r.r, r.z, z.(Ap - mean)) -- the last two
-// only when z is formed here, the last only for the flexible beta.  Every FP64
-// operation counts on this GPU (2 FP64 FMA/clk/SM): the mean subtraction and
-// z.q are skipped when not needed.
+// One CG update, fused with both reductions around it:
+//  - alpha = r.z / (p.Ap - mean sum p) from the operator's totals (the last
+//    block of the operator kernel summed them), mean = sum(Ap)/N when zero_mean;
+//  - x += alpha p; r -= alpha (Ap - mean); Jacobi/none: z = D^-1 r (diag holds
+//    the inverse diagonal);
+//  - FORM_Z: the last block adds the partials (r.r, r.z, z.(Ap - mean)) in a
+//    fixed order and does beta, the convergence test and the iteration count;
+//    otherwise (separate preconditioner) it leaves (r.r) partials for k_beta.
+// Every FP64 operation counts on this GPU (2 FP64 FMA/clk/SM): the mean
+// subtraction and z.q are compiled out when not needed.
 template <bool FORM_Z, bool ZERO_MEAN, bool ZQ>
-__global__ void k_update(const Scalars* __restrict__ sc, long long n, double* __restrict__ x, double* r,
-                         const double* __restrict__ p, const double* __restrict__ ap, double* z,
-                         const double* __restrict__ diag, double* __restrict__ part) {
+__global__ void k_update(Scalars* sc, long long n, double* __restrict__ x, double* r, const double* __restrict__ p,
+                         const double* __restrict__ ap, double* z, const double* __restrict__ diag,
+                         double* __restrict__ part, int flexible) {
   if (sc->done) return;
-  const double alpha = sc->alpha, mean = sc->mean;
-  double rr = 0.0, rz = 0.0, zq = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+  const double mean = ZERO_MEAN ? sc->tot[1] / sc->ntot : 0.0;
+  const double pap = sc->tot[0] - mean * sc->tot[2];
+  if (!finite(pap) || !(pap > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->done = finite(pap) ? BREAKDOWN : NONFINITE;
+    return;
+  }
+  const double rz_old = sc->rz;
+  const double alpha = rz_old / pap;
+  // |r|^2 only feeds the stopping test: it is accumulated in FP32 from the top
+  // 24 bits of r (relative accuracy ~1e-6 on a norm compared with rtol), which
+  // keeps the FP64 pipe for x, r, z and r.z.  Two elements per step (128-bit
+  // accesses) when the vectors are 16-byte aligned and n is even.
+  float rr32 = 0.f;
+  double rz = 0.0, zq = 0.0;
+  auto one = [&](long long i) {
     const double q = ZERO_MEAN ? ap[i] - mean : ap[i];
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q, r[i]);
     r[i] = ri;
-    rr = fma(ri, ri, rr);
+    const float rf = f64_top24(ri);
+    rr32 = fmaf(rf, rf, rr32);
     if (FORM_Z) {
       const double zi = diag ? ri * diag[i] : ri;
       if (z != r) z[i] = zi;
       rz = fma(ri, zi, rz);
       if (ZQ) zq = fma(zi, q, zq);
     }
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool vec = ((n & 1) == 0) && !(((unsigned long long)x | (unsigned long long)r | (unsigned long long)p |
+                                        (unsigned long long)ap | (unsigned long long)(z ? z : r) |
+                                        (unsigned long long)(diag ? diag : r)) & 15ull);
+  if (vec) {
+    for (long long j = t0; j < n / 2; j += stride) {
+      const double2 xv = reinterpret_cast<const double2*>(x)[j], pv = reinterpret_cast<const double2*>(p)[j];
+      const double2 rv = reinterpret_cast<const double2*>(r)[j], av = reinterpret_cast<const double2*>(ap)[j];
+      double2 dv = make_double2(1.0, 1.0);
+      if (FORM_Z && diag) dv = reinterpret_cast<const double2*>(diag)[j];
+      const double q0 = ZERO_MEAN ? av.x - mean : av.x, q1 = ZERO_MEAN ? av.y - mean : av.y;
+      const double r0 = fma(-alpha, q0, rv.x), r1 = fma(-alpha, q1, rv.y);
+      reinterpret_cast<double2*>(x)[j] = make_double2(fma(alpha, pv.x, xv.x), fma(alpha, pv.y, xv.y));
+      reinterpret_cast<double2*>(r)[j] = make_double2(r0, r1);
+      const float f0 = f64_top24(r0), f1 = f64_top24(r1);
+      rr32 = fmaf(f0, f0, fmaf(f1, f1, rr32));
+      if (FORM_Z) {
+        const double z0 = diag ? r0 * dv.x : r0, z1 = diag ? r1 * dv.y : r1;
+        if (z != r) reinterpret_cast<double2*>(z)[j] = make_double2(z0, z1);
+        rz = fma(r0, z0, fma(r1, z1, rz));
+        if (ZQ) zq = fma(z0, q0, fma(z1, q1, zq));
+      }
+    }
+  } else {
+    for (long long i = t0; i < n; i += stride) one(i);
   }
+  const double rr = (double)rr32;
   block_partial3(rr, rz, zq, part);
+  if (!FORM_Z) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc->alpha = alpha;
+      sc->mean = mean;
+    }
+    return;
+  }
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partial is visible before the count
+    last = atomicAdd(&sc->cnt_update, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+    a += __ldcg(part + 3 * i);
+    b += __ldcg(part + 3 * i + 1);
+    c += __ldcg(part + 3 * i + 2);
+  }
+  block_total3(a, b, c, sc->tot_update);
+  if (threadIdx.x == 0) {
+    const double rr_t = sc->tot_update[0], rz_t = sc->tot_update[1], zq_t = sc->tot_update[2];
+    const int it = sc->iters + 1;
+    sc->iters = it;
+    sc->alpha = alpha;
+    sc->mean = mean;
+    sc->rr = rr_t;
+    const double beta = flexible ? -alpha * zq_t / rz_old : rz_t / rz_old;
+    if (sc->record && it - 1 < kMaxLanczos) {
+      sc->lan_alpha[it - 1] = alpha;
+      sc->lan_beta[it - 1] = beta;
+    }
+    if (!finite(rr_t) || !finite(rz_t)) {
+      sc->done = NONFINITE;
+    } else if (rr_t <= sc->tol2 * sc->bb) {
+      sc->done = CONVERGED;
+    } else if (it >= sc->maxit) {
+      sc->done = MAXIT;
+    }
+    sc->beta = beta;
+    sc->rz = rz_t;
+    sc->cnt_update = 0u;
+  }
 }
 
-using UpdateFn = void (*)(const Scalars*, long long, double*, double*, const double*, const double*, double*,
-                          const double*, double*);
+using UpdateFn = void (*)(Scalars*, long long, double*, double*, const double*, const double*, double*,
+                          const double*, double*, int);
 
 UpdateFn pick_update(bool form_z, bool zero_mean, bool zq) {
   if (!form_z) return zero_mean ? k_update<false, true, false> : k_update<false, false, false>;
@@ -498,6 +615,13 @@ struct Solver {
   }
 
   int apply64(const double* x, double* y, double* dots, int* nb) {
+    DotSink sink;
+    sink.partials = dots;
+    if (dots) {  // inside an iteration: the last block forms the totals; skip once the solver is done
+      sink.counter = &w.sc->cnt_apply;
+      sink.totals = w.sc->tot;
+      sink.skip = &w.sc->done;
+    }
     cudaEvent_t e0 = nullptr;
     if (m.profile) {
       if (ev_used >= (int)evs.size()) {
@@ -509,7 +633,7 @@ struct Solver {
       // during stream capture only an "external" record becomes a graph node
       cudaEventRecordWithFlags(evs[ev_used].first, s, capturing ? cudaEventRecordExternal : 0);
     }
-    int st = launch_apply<double>(m, x, y, ncomp, cm, nu, nu_cell, true, dots, nb, s);
+    int st = launch_apply<double>(m, x, y, ncomp, cm, nu, nu_cell, true, dots ? &sink : nullptr, nb, s);
     if (m.profile) {
       cudaEventRecordWithFlags(evs[ev_used].second, s, capturing ? cudaEventRecordExternal : 0);
       ++ev_used;
@@ -564,14 +688,12 @@ struct Solver {
   int iteration() {
     int st, nb;
     if ((st = apply64(w.p, w.ap, w.part1, &nb))) return st;
-    k_alpha<<<1, kRedThreads, 0, s>>>(w.sc, w.part1, nb, o.zero_mean);
-    if ((st = launched())) return st;
     const bool sep = separate_precond();
     const double* dg = o.precond == SIPG_PC_JACOBI ? w.diag : nullptr;
     double* z = (o.precond == SIPG_PC_NONE) ? w.r : w.z;
     const int flex = o.precond == SIPG_PC_CHEB_F32 || (o.flexible && o.precond != SIPG_PC_INVMASS);
     pick_update(!sep, o.zero_mean != 0, flex != 0)<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, xcur, w.r, w.p, w.ap,
-                                                                                      z, dg, w.part1);
+                                                                                      z, dg, w.part1, flex);
     if ((st = launched())) return st;
     int nb2 = kVecBlocks;
     if (o.precond == SIPG_PC_INVMASS) {
@@ -582,9 +704,12 @@ struct Solver {
     } else if (o.precond == SIPG_PC_CHEB_F32) {
       if ((st = cheb_apply(w.z, w.r, w.ap, w.sc))) return st;
     }
-    // flexible beta needs z.(Ap - mean); the inverse-mass path uses the standard beta
-    k_beta<<<1, kRedThreads, 0, s>>>(w.sc, w.part1, kVecBlocks, sep ? w.part2 : nullptr, nb2, flex);
-    if ((st = launched())) return st;
+    // with a separate preconditioner, beta and the convergence test need its
+    // partials: one reduction kernel (the Jacobi / none path did them in k_update)
+    if (sep) {
+      k_beta<<<1, kRedThreads, 0, s>>>(w.sc, w.part1, kVecBlocks, w.part2, nb2, flex);
+      if ((st = launched())) return st;
+    }
     k_pupdate<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, w.p, z, 0);
     return launched();
   }

@@ -20,7 +20,7 @@ namespace sipg {
 using ::fma;  // keep the float / double overloads visible next to the double-float one
 #endif
 
-struct dfl {
+struct __align__(8) dfl {  // 8-byte aligned: one 64-bit load or store per value
   float hi, lo;
   __host__ __device__ constexpr dfl() : hi(0.f), lo(0.f) {}
   __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}

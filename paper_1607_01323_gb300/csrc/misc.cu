@@ -8,16 +8,26 @@ namespace {
 template <int P>
 int launch_inverse_mass_p(const Mesh& m, const double* x, double* y, int ncomp, double* dots, cudaStream_t s) {
   const int cpb = m.cpb[0] > 0 ? m.cpb[0] : default_cpb(P, 0);
-  const Geo<double> g = make_geo<double>(m);
   const dim3 grid((unsigned)((m.ncell + cpb - 1) / cpb), (unsigned)ncomp);
   const size_t smem = (size_t)cpb * P * P * P * sizeof(double);
   const int threads = (cpb * P * P + 31) / 32 * 32;  // whole warps
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
-  if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
-    cudaError_t e = cudaFuncSetAttribute(inverse_mass_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(inverse mass)");
+  // same arithmetic choice as the operator (double-float keeps FP64 data)
+  if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
+    if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
+      cudaError_t e = cudaFuncSetAttribute(inverse_mass_kernel<dfl, double, P>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(inverse mass)");
+    }
+    inverse_mass_kernel<dfl, double, P><<<grid, threads, smem, s>>>(make_geo<dfl>(m), x, y, cpb, dots);
+  } else {
+    if (smem + 2048 > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(inverse_mass_kernel<double, double, P>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(inverse mass)");
+    }
+    inverse_mass_kernel<double, double, P><<<grid, threads, smem, s>>>(make_geo<double>(m), x, y, cpb, dots);
   }
-  inverse_mass_kernel<P><<<grid, threads, smem, s>>>(g, x, y, cpb, dots);
   const_cast<Mesh&>(m).launches++;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "inverse mass kernel launch");

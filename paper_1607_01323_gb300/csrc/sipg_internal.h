@@ -106,19 +106,30 @@ int build_tables(Mesh& m);
 template <typename T>
 Geo<T> make_geo(const Mesh& m);
 
+// Where an operator kernel sends its dot products (x.y, sum y, sum x):
+// per-block partials to partials[3 * block]; if counter is set, the last block
+// to finish adds all partials in a fixed order into totals[0..2] and resets the
+// counter (no waiting: each block only increments it once).  If skip is set
+// and *skip != 0 the kernel returns at once (a finished solver's flag).
+struct DotSink {
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  double* totals = nullptr;
+  const int* skip = nullptr;
+};
+
 // Operator apply: y = mass_coef M x + nu (L x) [stiffness on/off]; nu_cell
-// replaces nu when not null.  If dots != null, per-block partial sums
-// (x.y, sum y, sum x) are written to dots[3 * block] and the number of blocks
-// to *nblocks.
+// replaces nu when not null.  Dot products go to `sink` (may be null); the
+// number of blocks is written to *nblocks.
 template <typename T>
 int launch_apply(const Mesh& m, const T* x, T* y, int ncomp, T mass_coef, T nu, const T* nu_cell, bool stiffness,
-                 double* dots, int* nblocks, cudaStream_t s);
+                 const DotSink* sink, int* nblocks, cudaStream_t s);
 template <>
 int launch_apply<double>(const Mesh& m, const double* x, double* y, int ncomp, double mass_coef, double nu,
-                         const double* nu_cell, bool stiffness, double* dots, int* nblocks, cudaStream_t s);
+                         const double* nu_cell, bool stiffness, const DotSink* sink, int* nblocks, cudaStream_t s);
 template <>
 int launch_apply<float>(const Mesh& m, const float* x, float* y, int ncomp, float mass_coef, float nu,
-                        const float* nu_cell, bool stiffness, double* dots, int* nblocks, cudaStream_t s);
+                        const float* nu_cell, bool stiffness, const DotSink* sink, int* nblocks, cudaStream_t s);
 
 int launch_inverse_mass(const Mesh& m, const double* x, double* y, int ncomp, double* dots, const double* rdot,
                         cudaStream_t s);

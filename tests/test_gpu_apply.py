@@ -172,6 +172,21 @@ def test_mass_inverse_mass_diagonal():
         assert np.allclose(d, op.diagonal(mass_coef=1500.0, nu_cell=nu_cell), rtol=1e-13, atol=0)
 
 
+@pytest.mark.parametrize("k", [1, 3, 5, 7])
+def test_inverse_mass_double_float(k):
+    """The tensorial inverse mass in double-float arithmetic matches the oracle's
+    per-element Cholesky solve to 1e-12 (relative to the largest output)."""
+    from paper_1607_01323_gb300 import apply_inverse_mass_f64
+    c = channel((3, 4, 2))
+    op = SIPG(oracle_spec(c), k)
+    m = gpu_mesh(c, k)
+    m.set_f64_arithmetic("double_float")
+    x = uniform(2 * m.n_dofs, "x")
+    y = apply_inverse_mass_f64(m, _cuda(x)).cpu().numpy()
+    y_ref = op.inverse_mass_apply(x)
+    assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
+
+
 def test_geometry_matches_oracle():
     for c, k in [(channel((3, 6, 2), gamma=2.25), 4), (case((2, 2, 3), lo=(-1, 0, 2), hi=(1, 3, 5)), 2)]:
         op = SIPG(oracle_spec(c), k)
