@@ -447,6 +447,7 @@ def run_config(args):
         y = torch.empty_like(x)
         t, _ = _timed(lambda: [apply_laplace_f64(m, x, y) for _ in range(100)], reps=5)
         out["apply_f64"] = {"us": 1e6 * t / 100, "dofs": m.n_dofs, "note": "launch-latency bound (64 cells)"}
+    elif args.workload == "c3":
         m = Mesh((64, 64, 64), w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping="channel", gamma=1.8, k=3)
         m.set_f64_arithmetic(args.f64)
         N = m.n_dofs

@@ -231,16 +231,16 @@ int sipg_adjoint_grad_nu(const sipg_mesh* mesh, const double* nu_cell, const dou
  * file (one "key value" line per (k, precision, map, mesh size)). */
 int sipg_autotune(sipg_mesh* mesh, int precision, const char* cache_path);
 
-/* Arithmetic of the FP64 operator entry points for a uniform viscosity
- * (sipg_apply_laplace_f64, sipg_apply_helmholtz_f64 with nu_cell == NULL, and
- * the operator inside sipg_cg_solve).  SIPG_F64_NATIVE (default) computes in
+/* Arithmetic of the FP64 operator entry points (sipg_apply_laplace_f64,
+ * sipg_apply_helmholtz_f64 and the operator inside sipg_cg_solve).  SIPG_F64_NATIVE (default) computes in
  * FP64.  SIPG_F64_DOUBLE_FLOAT keeps the FP64 data in memory but evaluates the
  * sum-factorised operator in double-float arithmetic (pairs of FP32 with exact
  * product errors and TwoSum, about 2^-46 relative per operation) on the FP32
  * pipes, which issue 64 times the FP64 rate on GB300; results stay within the
  * FP64 parity tolerance (1e-12 of ||A|| ||x||).  The same choice applies to
- * sipg_apply_inverse_mass_f64 (and the inverse-mass preconditioner).  The
- * per-cell-viscosity operator, the mass and adjoint kernels always use FP64. */
+ * sipg_apply_inverse_mass_f64 (and the inverse-mass preconditioner), to the
+ * per-cell-viscosity Helmholtz operator and to sipg_apply_mass_f64; the
+ * diagonal and the adjoint-gradient kernels always use FP64. */
 int sipg_set_f64_arithmetic(sipg_mesh* mesh, int mode);
 int sipg_get_f64_arithmetic(const sipg_mesh* mesh, int* mode);
 

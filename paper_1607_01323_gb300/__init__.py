@@ -117,8 +117,8 @@ class Mesh:
         return out
 
     def set_f64_arithmetic(self, mode):
-        """'native' (FP64) or 'double_float' (FP32 pairs) for the FP64 operator
-        with a uniform viscosity."""
+        """'native' (FP64) or 'double_float' (FP32 pairs) arithmetic for the FP64
+        operator, mass and inverse-mass applies (FP64 data either way)."""
         L.check(L.lib().sipg_set_f64_arithmetic(self._h, {"native": 0, "double_float": 1}[mode]))
         self.f64_arithmetic = mode
 

@@ -230,6 +230,12 @@ __device__ __forceinline__ void load_line_global(T (&v)[P], const T* __restrict_
   for (int a = 0; a < P; ++a) v[a] = __ldg(base + start + a * step);
 }
 
+template <typename T, typename S, int P>
+__device__ __forceinline__ void load_line_global_cvt(T (&v)[P], const S* __restrict__ base, int start, int step) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) v[a] = cvt_in<T, S>(__ldg(base + start + a * step));
+}
+
 template <typename T, int P>
 __device__ __forceinline__ void store_line(T* base, const T (&v)[P], int start, int step) {
 #pragma unroll
@@ -314,9 +320,9 @@ struct DirCtx {
   T nuL, nuR, tauFL, tauFR;
 };
 
-template <typename T, int P>
+template <typename T, int P, typename S>
 __device__ __forceinline__ DirCtx<T, P> dir_ctx(const Geo<T>& g, int dir, const int (&id)[3], int e, T nue, T tau_e,
-                                                const T* __restrict__ nu_cell, T nu) {
+                                                const S* __restrict__ nu_cell, T nu) {
   using O = LayerOff<P>;
   DirCtx<T, P> c;
   c.L = g.tab[dir] + id[dir] * O::stride;
@@ -330,24 +336,27 @@ __device__ __forceinline__ DirCtx<T, P> dir_ctx(const Geo<T>& g, int dir, const 
   c.tauFL = c.tauFR = tau_e;
   if (c.kindL == 0) {
     c.LL = g.tab[dir] + jl * O::stride;
-    c.nuL = nu_cell ? __ldg(nu_cell + c.nbL) : nu;
+    c.nuL = nu_cell ? cvt_in<T, S>(__ldg(nu_cell + c.nbL)) : nu;
     const T tn = tau_e + g.tau_scale * (c.LL[O::t] - t_own);
     c.tauFL = tn > tau_e ? tn : tau_e;
   }
   if (c.kindR == 0) {
     c.LR = g.tab[dir] + jr * O::stride;
-    c.nuR = nu_cell ? __ldg(nu_cell + c.nbR) : nu;
+    c.nuR = nu_cell ? cvt_in<T, S>(__ldg(nu_cell + c.nbR)) : nu;
     const T tn = tau_e + g.tau_scale * (c.LR[O::t] - t_own);
     c.tauFR = tn > tau_e ? tn : tau_e;
   }
   return c;
 }
 
-// y = mass_coef M x + nu L x for CPB cells per block, p^2 threads per cell.
-template <typename T, int P>
-__global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const T* __restrict__ x, T* __restrict__ y, int cpb,
-                                                     T mass_coef, T nu, const T* __restrict__ nu_cell, int stiffness,
-                                                     DotSink sink) {
+// y = mass_coef M x + nu L x for CPB cells per block, p^2 threads per cell
+// (per-cell viscosity or mass only).  T is the arithmetic, S the storage type
+// of x, y and nu_cell.
+template <typename T, typename S, int P>
+__global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const S* __restrict__ x, S* __restrict__ y,
+                                                                int cpb, T mass_coef, T nu,
+                                                                const S* __restrict__ nu_cell, int stiffness,
+                                                                DotSink sink) {
   if (sink.skip && *sink.skip) return;
   double* dots = sink.partials;
   constexpr int P2 = P * P, P3 = P * P * P;
@@ -362,11 +371,11 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
   const int e = (int)(cell0 + cs);
   const bool active = cs < cpb && e < g.ncell;  // blocks are rounded up to whole warps
   const long long cbase = (long long)blockIdx.y * g.ncell * P3;
-  const T* __restrict__ xc = x + cbase;
+  const S* __restrict__ xc = x + cbase;
   {
     const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
-    const T* xb = xc + cell0 * P3;
-    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = xb[idx];
+    const S* xb = xc + cell0 * P3;
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx]);
   }
   __syncthreads();
   T* us = su + cs * P3;
@@ -379,7 +388,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
     id[0] = e % g.n[0];
     id[1] = (e / g.n[0]) % g.n[1];
     id[2] = e / (g.n[0] * g.n[1]);
-    if (nu_cell) nue = __ldg(nu_cell + e);
+    if (nu_cell) nue = cvt_in<T, S>(__ldg(nu_cell + e));
     using O = LayerOff<P>;
     tau_e = g.tau_scale * (g.tab[0][id[0] * O::stride + O::t] + g.tab[1][id[1] * O::stride + O::t] +
                            g.tab[2][id[2] * O::stride + O::t]);
@@ -397,9 +406,9 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
         for (int a = 0; a < P; ++a) ux[a] = u[a];
       }
       if (stiff) {
-        DirCtx<T, P> c = dir_ctx<T, P>(g, dir, id, e, nue, tau_e, nu_cell, nu);
-        if (c.kindL == 0) load_line_global<T, P>(uL, xc + (long long)c.nbL * P3, start, step);
-        if (c.kindR == 0) load_line_global<T, P>(uR, xc + (long long)c.nbR * P3, start, step);
+        DirCtx<T, P> c = dir_ctx<T, P, S>(g, dir, id, e, nue, tau_e, nu_cell, nu);
+        if (c.kindL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)c.nbL * P3, start, step);
+        if (c.kindR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)c.nbR * P3, start, step);
         line_op<T, P>(w, u, c.L, nue, true, T(0), false, c.kindL, uL, c.LL, c.nuL, c.tauFL, c.kindR, uR, c.LR, c.nuR,
                       c.tauFR, tau_e);
       } else {
@@ -415,10 +424,10 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
     line_geom<P>(2, ti, tj, start, step);
     T u[P], uL[P], uR[P], w[P], v1[P], v2[P], a1[P], a2[P];
     load_line<T, P>(u, us, start, step);
-    DirCtx<T, P> c = dir_ctx<T, P>(g, 2, id, e, nue, tau_e, nu_cell, nu);
+    DirCtx<T, P> c = dir_ctx<T, P, S>(g, 2, id, e, nue, tau_e, nu_cell, nu);
     if (stiff) {
-      if (c.kindL == 0) load_line_global<T, P>(uL, xc + (long long)c.nbL * P3, start, step);
-      if (c.kindR == 0) load_line_global<T, P>(uR, xc + (long long)c.nbR * P3, start, step);
+      if (c.kindL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)c.nbL * P3, start, step);
+      if (c.kindR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)c.nbR * P3, start, step);
     }
     line_op<T, P>(w, u, c.L, nue, stiff, mass_coef, mass_coef != T(0), c.kindL, uL, c.LL, c.nuL, c.tauFL, c.kindR, uR,
                   c.LR, c.nuR, c.tauFR, tau_e);
@@ -456,19 +465,26 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
     load_line<T, P>(v, w2, start, step);
     matvec(out, Mx, v);
     load_line<T, P>(r1, w1, start, step);
-    T* yo = y + cbase + (long long)e * P3 + start;
+    S* yo = y + cbase + (long long)e * P3 + start;
 #pragma unroll
     for (int a = 0; a < P; ++a) {
       out[a] += r1[a];
-      yo[a] = out[a];
+      yo[a] = cvt_out<S, T>(out[a]);
     }
     if (dots) {
+      T sxy(0), sy(0), sx(0);
 #pragma unroll
-      for (int a = 0; a < P; ++a) {
-        d_xy += (double)out[a] * (double)ux[a];
-        d_y += (double)out[a];
-        d_x += (double)ux[a];
+      for (int a = 0; a < P; ++a) sxy = fma(out[a], ux[a], sxy);
+      if (sink.sums) {
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+          sy += out[a];
+          sx += ux[a];
+        }
       }
+      d_xy = cvt_out<double, T>(sxy);
+      d_y = cvt_out<double, T>(sy);
+      d_x = cvt_out<double, T>(sx);
     }
   }
   if (dots) sink_dots(sink, d_xy, d_y, d_x);
@@ -510,20 +526,15 @@ __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* _
 // y = scale * (L x + mass_rel M x) for a uniform viscosity: scale = nu,
 // mass_rel = mass_coef / nu (Laplace: scale 1, mass_rel 0).  Same phases as
 // apply_kernel with the precombined line operator.
-template <typename T, typename S, int P>
-__device__ __forceinline__ void load_line_global_cvt(T (&v)[P], const S* __restrict__ base, int start, int step) {
-#pragma unroll
-  for (int a = 0; a < P; ++a) v[a] = cvt_in<T, S>(__ldg(base + start + a * step));
-}
-
 // Blocks per SM requested from the register allocator: the double-float
 // kernel fits 80 registers without spills up to p = 5, which allows three
 // 256-thread blocks (24 warps) per SM; the FP32 kernel fits 64 registers (four
-// blocks) up to p = 6; native FP64 is FP64-issue-bound and keeps the default.
+// blocks) up to p = 6; native FP64 keeps two blocks (128 registers) up to p = 6
+// so that enough warps feed the FP64 pipe.
 template <typename T, int P>
 struct UniformMinBlocks {
   static constexpr int value = std::is_same<T, dfl>::value ? (P <= 5 ? 3 : 1)
-                               : (std::is_same<T, float>::value ? (P <= 6 ? 4 : (P == 7 ? 3 : 2)) : 1);
+                               : (std::is_same<T, float>::value ? (P <= 6 ? 4 : (P == 7 ? 3 : 2)) : (P <= 6 ? 2 : 1));
 };
 
 template <typename T, typename S, int P>
@@ -671,10 +682,13 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
       load_line_global_cvt<T, S, P>(ux, xc + (long long)e * P3, start, step);
       T sxy(0), sy(0), sx(0);
 #pragma unroll
-      for (int a = 0; a < P; ++a) {
-        sxy = fma(out[a], ux[a], sxy);
-        sy += out[a];
-        sx += ux[a];
+      for (int a = 0; a < P; ++a) sxy = fma(out[a], ux[a], sxy);
+      if (sink.sums) {  // sums of y and x only for the zero-mean projection
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+          sy += out[a];
+          sx += ux[a];
+        }
       }
       d_xy = cvt_out<double, T>(sxy);
       d_y = cvt_out<double, T>(sy);

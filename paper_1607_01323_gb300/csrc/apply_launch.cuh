@@ -23,7 +23,7 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
   if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
     cudaError_t e = uniform ? cudaFuncSetAttribute(apply_uniform_kernel<T, T, P>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                            : cudaFuncSetAttribute(apply_kernel<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            : cudaFuncSetAttribute(apply_kernel<T, T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
   }
@@ -48,7 +48,22 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
     }
     apply_uniform_kernel<T, T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm / nu, nu, do_scale, do_mass, ds);
   } else {
-    apply_kernel<T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm, nu, nu_cell, stiff ? 1 : 0, ds);
+    if constexpr (std::is_same<T, double>::value) {
+      if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
+        if (smem + 2048 > 48 * 1024) {
+          cudaError_t e = cudaFuncSetAttribute(apply_kernel<dfl, double, P>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
+        }
+        apply_kernel<dfl, double, P><<<grid, threads, smem, s>>>(make_geo<dfl>(m), x, y, cpb, dfl(cm), dfl(nu),
+                                                                 nu_cell, stiff ? 1 : 0, ds);
+        if (nblocks) *nblocks = (int)(grid.x * grid.y);
+        const_cast<Mesh&>(m).launches++;
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch");
+      }
+    }
+    apply_kernel<T, T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm, nu, nu_cell, stiff ? 1 : 0, ds);
   }
   if (nblocks) *nblocks = (int)(grid.x * grid.y);
   const_cast<Mesh&>(m).launches++;

@@ -621,6 +621,7 @@ struct Solver {
       sink.counter = &w.sc->cnt_apply;
       sink.totals = w.sc->tot;
       sink.skip = &w.sc->done;
+      sink.sums = o.zero_mean ? 1 : 0;
     }
     cudaEvent_t e0 = nullptr;
     if (m.profile) {

@@ -116,6 +116,7 @@ struct DotSink {
   unsigned* counter = nullptr;
   double* totals = nullptr;
   const int* skip = nullptr;
+  int sums = 1;  // 0: only x.y is needed (sum y, sum x are left 0)
 };
 
 // Operator apply: y = mass_coef M x + nu (L x) [stiffness on/off]; nu_cell

@@ -82,6 +82,25 @@ def test_laplace_f64_double_float_parity(name, c, k, pen):
     assert scaled_err(y, H @ x[:N], abs(H).sum(axis=1).max(), x[:N]) <= TOL64
 
 
+@pytest.mark.parametrize("k", [2, 3, 5])
+def test_helmholtz_nu_cell_and_mass_double_float(k):
+    """Per-cell viscosity and mass-only applies in double-float keep the 1e-12 bar."""
+    from paper_1607_01323_gb300 import apply_helmholtz_f64, apply_mass_f64
+    c = channel((3, 4, 2))
+    op = SIPG(oracle_spec(c), k)
+    m = gpu_mesh(c, k)
+    m.set_f64_arithmetic("double_float")
+    N = m.n_dofs
+    x = uniform(N, "x")
+    nu_cell = np.exp(0.5 * inputs.normal(0, "xi", m.ncell)) / 180.0
+    A = op.assemble(mass_coef=1500.0, nu_cell=nu_cell)
+    y = apply_helmholtz_f64(m, _cuda(x), 1500.0, 0.0, nu_cell=_cuda(nu_cell)).cpu().numpy()
+    assert scaled_err(y, A @ x, abs(A).sum(axis=1).max(), x) <= TOL64
+    Mm = op.assemble(mass_coef=1.0, stiffness=False)
+    ym = apply_mass_f64(m, _cuda(x)).cpu().numpy()
+    assert scaled_err(ym, Mm @ x, abs(Mm).sum(axis=1).max(), x) <= TOL64
+
+
 def test_double_float_dynamic_range():
     """Inputs spanning many orders of magnitude (and exact zeros) keep the
     1e-12 scaled bar in double-float."""
