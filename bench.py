@@ -122,6 +122,21 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def aggregate_replicas(t_local, units_local, dist=None):
+    """Whole-job throughput of independent replicas: the units of all ranks
+    over the slowest rank's time (max over ranks).  Returns (value, t_max)."""
+    import torch
+    world = dist.get_world_size() if dist is not None and dist.is_initialized() else 1
+    if world > 1:
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(t_local)], device=dev, dtype=torch.float64)
+        u = torch.tensor([float(units_local)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        return u.item() / t.item(), t.item()
+    return units_local / t_local, t_local
+
+
 def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -274,13 +289,8 @@ def run_ours(args):
     apply_ms, applies, launches = m.profile_read(reset=True)
     m.profile_enable(False)
     t_steps = [a.elapsed_time(bb) for a, bb in ev]
-    t_total = sum(t_steps) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = tt.item()
     n_applies = sum(it + 1 for it in iters)  # initial residual + one per iteration
-    value = world * n_applies * N / t_total
+    value, t_total = aggregate_replicas(sum(t_steps) / 1e3, n_applies * N, dist if world > 1 else None)
     ms_per_step = 1e3 * t_total / args.steps
 
     # end to end through the public API: pinned host rhs -> device, solve, solution -> host

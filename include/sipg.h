@@ -244,6 +244,16 @@ int sipg_autotune(sipg_mesh* mesh, int precision, const char* cache_path);
 int sipg_set_f64_arithmetic(sipg_mesh* mesh, int mode);
 int sipg_get_f64_arithmetic(const sipg_mesh* mesh, int* mode);
 
+/* Thread mapping of the FP32 operator with a uniform viscosity:
+ * SIPG_THREADS_LINE (default: p^2 threads per cell, one line each) or
+ * SIPG_THREADS_PLANE (p threads per cell, one plane of p lines each, so that
+ * every 1D matrix is loaded once per p lines; slower on GB300 at k = 4, 5 in
+ * our measurements, kept for the autotuner).  Same results.  Resets the FP32 cells
+ * per block to the mapping's default; sipg_autotune(precision 1) searches both
+ * mappings. */
+typedef enum { SIPG_THREADS_LINE = 0, SIPG_THREADS_PLANE = 1 } sipg_threads;
+int sipg_set_f32_mapping(sipg_mesh* mesh, int mapping);
+
 /* Cells per block currently used for a precision (host output). */
 int sipg_get_cells_per_block(const sipg_mesh* mesh, int precision, int* cpb);
 int sipg_set_cells_per_block(sipg_mesh* mesh, int precision, int cpb);

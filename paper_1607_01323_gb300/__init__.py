@@ -122,6 +122,11 @@ class Mesh:
         L.check(L.lib().sipg_set_f64_arithmetic(self._h, {"native": 0, "double_float": 1}[mode]))
         self.f64_arithmetic = mode
 
+    def set_f32_mapping(self, mapping):
+        """'line' (p^2 threads per cell) or 'plane' (p threads per cell) for the
+        FP32 operator with a uniform viscosity."""
+        L.check(L.lib().sipg_set_f32_mapping(self._h, {"line": 0, "plane": 1}[mapping]))
+
     def cells_per_block(self, precision=0):
         v = C.c_int()
         L.check(L.lib().sipg_get_cells_per_block(self._h, int(precision), C.byref(v)))

@@ -62,6 +62,7 @@ _SIGS = {
     "sipg_autotune": [C.c_void_p, C.c_int, C.c_char_p],
     "sipg_set_f64_arithmetic": [C.c_void_p, C.c_int],
     "sipg_get_f64_arithmetic": [C.c_void_p, C.POINTER(C.c_int)],
+    "sipg_set_f32_mapping": [C.c_void_p, C.c_int],
     "sipg_get_cells_per_block": [C.c_void_p, C.c_int, C.POINTER(C.c_int)],
     "sipg_set_cells_per_block": [C.c_void_p, C.c_int, C.c_int],
     "sipg_profile_enable": [C.c_void_p, C.c_int],

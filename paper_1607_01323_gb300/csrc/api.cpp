@@ -82,6 +82,19 @@ int default_cpb(int p, int precision) {
   }
 }
 
+// Plane mapping (P threads per cell): as many cells as fit 256 threads and
+// about 100 KB of shared memory (three FP32 buffers of p^3 per cell).
+int default_cpb_plane(int p) {
+  int c = 256 / p;
+  const int smem_cap = 100 * 1024 / (3 * p * p * p * 4);
+  return c < smem_cap ? c : smem_cap;
+}
+
+int cells_per_block(const Mesh& m, int precision) {
+  if (m.cpb[precision] > 0) return m.cpb[precision];
+  return (precision == 1 && m.f32_mapping == 1) ? default_cpb_plane(m.p) : default_cpb(m.p, precision);
+}
+
 void prof_begin(Mesh& m, cudaStream_t s, cudaEvent_t* e0) {
   *e0 = nullptr;
   if (!m.profile) return;
@@ -470,7 +483,16 @@ int sipg_get_cells_per_block(const sipg_mesh* m, int precision, int* cpb) {
   int st;
   if ((st = check_mesh(m))) return st;
   if (!cpb || (precision != 0 && precision != 1)) return fail(SIPG_EINVAL, "bad argument");
-  *cpb = m->cpb[precision] > 0 ? m->cpb[precision] : default_cpb(m->p, precision);
+  *cpb = cells_per_block(*m, precision);
+  return SIPG_OK;
+}
+
+int sipg_set_f32_mapping(sipg_mesh* m, int mapping) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (mapping != SIPG_THREADS_LINE && mapping != SIPG_THREADS_PLANE) return fail(SIPG_EINVAL, "unknown mapping");
+  m->f32_mapping = mapping;
+  m->cpb[1] = 0;
   return SIPG_OK;
 }
 
@@ -520,9 +542,14 @@ int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
   int best = 0;
   float best_ms = 1e30f;
   const int old = m->cpb[precision];
-  for (int c = 1; c <= 64; ++c) {
+  const int old_map = m->f32_mapping;
+  int best_map = old_map;
+  for (int cand = 0; cand < (precision == 1 ? 2 * 128 : 128); ++cand) {
+    const int c = cand % 128 + 1;
+    if (precision == 1) m->f32_mapping = cand < 128 ? 0 : 1;  // FP32: both thread mappings
     // every feasible count whose block wastes at most 1/8 of its lanes
-    const int thr = c * m->p * m->p, rounded = (thr + 31) / 32 * 32;
+    const int per_cell = (precision == 1 && m->f32_mapping == 1) ? m->p : m->p * m->p;
+    const int thr = c * per_cell, rounded = (thr + 31) / 32 * 32;
     if (8 * (rounded - thr) > rounded) continue;
     if (sipg_set_cells_per_block(m, precision, c) != SIPG_OK) continue;
     float tot = 0.f;
@@ -545,8 +572,10 @@ int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
     if (ok && tot < best_ms) {
       best_ms = tot;
       best = c;
+      best_map = m->f32_mapping;
     }
   }
+  m->f32_mapping = best_map;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(x);
@@ -554,6 +583,7 @@ int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
   cudaGetLastError();
   if (best == 0) {
     m->cpb[precision] = old;
+    m->f32_mapping = old_map;
     return fail(SIPG_ECUDA, "autotune: no candidate ran");
   }
   m->cpb[precision] = best;

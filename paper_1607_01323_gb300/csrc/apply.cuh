@@ -528,12 +528,13 @@ __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* _
 // apply_kernel with the precombined line operator.
 // Blocks per SM requested from the register allocator: the double-float
 // kernel fits 80 registers without spills up to p = 5, which allows three
-// 256-thread blocks (24 warps) per SM; the FP32 kernel fits 64 registers (four
+// 256-thread blocks (24 warps) per SM, and 128 (two blocks) up to p = 7; the
+// FP32 kernel fits 64 registers (four
 // blocks) up to p = 6; native FP64 keeps two blocks (128 registers) up to p = 6
 // so that enough warps feed the FP64 pipe.
 template <typename T, int P>
 struct UniformMinBlocks {
-  static constexpr int value = std::is_same<T, dfl>::value ? (P <= 5 ? 3 : 1)
+  static constexpr int value = std::is_same<T, dfl>::value ? (P <= 5 ? 3 : (P <= 7 ? 2 : 1))
                                : (std::is_same<T, float>::value ? (P <= 6 ? 4 : (P == 7 ? 3 : 2)) : (P <= 6 ? 2 : 1));
 };
 
@@ -696,6 +697,207 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     }
   }
   if (dots) sink_dots(sink, d_xy, d_y, d_x);
+}
+
+// Plane variant of the uniform-viscosity operator for FP32 (the line variant
+// issues one load of a 1D-matrix entry per FMA; measured slower on GB300 at
+// k = 4, 5 -- less parallelism per cell -- and kept as an autotuner candidate).
+// P threads per cell; thread t owns the plane c = t in the phases along x and
+// y (X, Y, Y2, X2) and the plane b = t in the phase along z, and loads each
+// phase's 1D matrices once into registers for its P lines: P times fewer
+// table loads.  Same arithmetic and results as apply_uniform_kernel.
+template <typename T, int P>
+__device__ __forceinline__ void load_mat(T (&A)[P * P], const T* __restrict__ src) {
+#pragma unroll
+  for (int i = 0; i < P * P; ++i) A[i] = src[i];
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void matvec_reg(T (&out)[P], const T (&A)[P * P], const T (&v)[P]) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < P; ++b) s = fma(A[a * P + b], v[b], s);
+    out[a] = s;
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kMaxCellThreads) apply_plane_kernel(Geo<T> g, const T* __restrict__ x,
+                                                                      T* __restrict__ y, int cpb, T mass_rel,
+                                                                      T scale, int do_scale, int do_mass) {
+  using O = LayerOff<P>;
+  constexpr int P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);
+  T* s1 = su + cpb * P3;
+  T* s2 = s1 + cpb * P3;
+  const int cs = threadIdx.x / P;
+  const int t = threadIdx.x - cs * P;
+  const long long cell0 = (long long)blockIdx.x * cpb;
+  const int e = (int)(cell0 + cs);
+  const bool active = cs < cpb && e < g.ncell;
+  const long long cbase = (long long)blockIdx.y * g.ncell * P3;
+  const T* __restrict__ xc = x + cbase;
+  const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
+  for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = xc[cell0 * P3 + idx];
+  __syncthreads();
+  T* us = su + cs * P3;
+  T* w1 = s1 + cs * P3;
+  T* w2 = s2 + cs * P3;
+  int id[3] = {0, 0, 0};
+  T tau_e = T(0);
+  if (active) {
+    id[0] = e % g.n[0];
+    id[1] = (e / g.n[0]) % g.n[1];
+    id[2] = e / (g.n[0] * g.n[1]);
+    tau_e = g.tab[0][id[0] * O::stride + O::ts] + g.tab[1][id[1] * O::stride + O::ts] +
+            g.tab[2][id[2] * O::stride + O::ts];
+  }
+  const T tau2e = tau_e + tau_e;
+  // neighbour line: from shared memory when staged in this block (phases X, Y
+  // only: the input stays unchanged there), else from global memory
+  auto nb_line = [&](T (&v)[P], int nb, int start, int step, bool smem_ok) {
+    const long long sl = (long long)nb - cell0;
+    if (smem_ok && sl >= 0 && sl < nc)
+      load_line<T, P>(v, su + sl * P3, start, step);
+    else
+      load_line_global<T, P>(v, xc + (long long)nb * P3, start, step);
+  };
+  if (active) {
+    // phases X and Y on the plane c = t
+#pragma unroll 1
+    for (int dir = 0; dir < 2; ++dir) {
+      const T* L = g.tab[dir] + id[dir] * O::stride;
+      int nbL, nbR, kL, kR, jl, jr;
+      face_neighbor(g, dir, 0, id[dir], e, nbL, kL, jl);
+      face_neighbor(g, dir, 1, id[dir], e, nbR, kR, jr);
+      const T* LL = kL == 0 ? g.tab[dir] + jl * O::stride : L;
+      const T* LR = kR == 0 ? g.tab[dir] + jr * O::stride : L;
+      T Kc[P * P], dRh[P], dLh[P], nLh[P], nRh[P];
+      load_mat<T, P>(Kc, L + O::Kc);
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        dRh[a] = L[O::dRh + a];
+        dLh[a] = L[O::dLh + a];
+        nLh[a] = LR[O::dLh + a];  // right neighbour's low-end half derivative
+        nRh[a] = LL[O::dRh + a];  // left neighbour's high-end half derivative
+      }
+      const T tFL = tau_e + L[O::dTL], tFR = tau_e + L[O::dTR];
+#pragma unroll 1
+      for (int q = 0; q < P; ++q) {
+        int start, step;
+        line_geom<P>(dir, q, t, start, step);  // x-line (b=q, c=t) or y-line (a=q, c=t)
+        T u[P], uL[P], uR[P], w[P];
+        load_line<T, P>(u, us, start, step);
+        if (kL == 0) nb_line(uL, nbL, start, step, true);
+        if (kR == 0) nb_line(uR, nbR, start, step, true);
+        matvec_reg<T, P>(w, Kc, u);
+        if (kR == 0) {
+          T gn = T(0);
+#pragma unroll
+          for (int a = 0; a < P; ++a) gn = fma(nLh[a], uR[a], gn);
+          w[P - 1] += fma(tFR, u[P - 1] - uR[0], -gn);
+#pragma unroll
+          for (int a = 0; a < P; ++a) w[a] = fma(dRh[a], uR[0], w[a]);
+        } else if (kR == SIPG_BC_DIRICHLET) {
+          w[P - 1] = fma(tau2e, u[P - 1], w[P - 1]);
+        }
+        if (kL == 0) {
+          T gn = T(0);
+#pragma unroll
+          for (int a = 0; a < P; ++a) gn = fma(nRh[a], uL[a], gn);
+          w[0] += fma(-tFL, uL[P - 1] - u[0], gn);
+#pragma unroll
+          for (int a = 0; a < P; ++a) w[a] = fma(dLh[a], -uL[P - 1], w[a]);
+        } else if (kL == SIPG_BC_DIRICHLET) {
+          w[0] = fma(tau2e, u[0], w[0]);
+        }
+        store_line<T, P>(dir == 0 ? w1 : w2, w, start, step);
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    // phase Z on the plane b = t: w_z, Mz w_x, Mz w_y (each thread only touches
+    // its own z-lines)
+    const T* L = g.tab[2] + id[2] * O::stride;
+    int nbL, nbR, kL, kR, jl, jr;
+    face_neighbor(g, 2, 0, id[2], e, nbL, kL, jl);
+    face_neighbor(g, 2, 1, id[2], e, nbR, kR, jr);
+    const T* LL = kL == 0 ? g.tab[2] + jl * O::stride : L;
+    const T* LR = kR == 0 ? g.tab[2] + jr * O::stride : L;
+    T Mz[P * P];
+    load_mat<T, P>(Mz, L + O::M);
+#pragma unroll 1
+    for (int q = 0; q < P; ++q) {
+      int start, step;
+      line_geom<P>(2, q, t, start, step);  // z-line (a=q, b=t)
+      T v[P], r[P];
+      load_line<T, P>(v, w1, start, step);
+      matvec_reg<T, P>(r, Mz, v);
+      store_line<T, P>(w1, r, start, step);
+      load_line<T, P>(v, w2, start, step);
+      matvec_reg<T, P>(r, Mz, v);
+      store_line<T, P>(w2, r, start, step);
+      T u[P], uL[P], uR[P], w[P];
+      load_line<T, P>(u, us, start, step);
+      if (kL == 0) nb_line(uL, nbL, start, step, false);
+      if (kR == 0) nb_line(uR, nbR, start, step, false);
+      line_op_u<T, P>(w, u, L, kL, uL, LL, tau_e + L[O::dTL], kR, uR, LR, tau_e + L[O::dTR], tau2e);
+      if (do_mass) {
+        T mu[P];
+        matvec_reg<T, P>(mu, Mz, u);
+#pragma unroll
+        for (int a = 0; a < P; ++a) w[a] = fma(mass_rel, mu[a], w[a]);
+      }
+      store_line<T, P>(us, w, start, step);
+    }
+  }
+  __syncthreads();
+  if (active) {
+    // phase Y2 on the plane c = t
+    T My[P * P];
+    load_mat<T, P>(My, g.tab[1] + id[1] * O::stride + O::M);
+#pragma unroll 1
+    for (int q = 0; q < P; ++q) {
+      int start, step;
+      line_geom<P>(1, q, t, start, step);
+      T v[P], r[P];
+      load_line<T, P>(v, w1, start, step);
+      matvec_reg<T, P>(r, My, v);
+      store_line<T, P>(w1, r, start, step);
+      load_line<T, P>(v, us, start, step);
+      matvec_reg<T, P>(r, My, v);
+      load_line<T, P>(v, w2, start, step);
+#pragma unroll
+      for (int a = 0; a < P; ++a) r[a] += v[a];
+      store_line<T, P>(w2, r, start, step);
+    }
+  }
+  __syncthreads();
+  if (active) {
+    // phase X2 on the plane c = t: y = Mx R2 + R1 -> global
+    T Mx[P * P];
+    load_mat<T, P>(Mx, g.tab[0] + id[0] * O::stride + O::M);
+#pragma unroll 1
+    for (int q = 0; q < P; ++q) {
+      int start, step;
+      line_geom<P>(0, q, t, start, step);
+      T v[P], out[P], r1[P];
+      load_line<T, P>(v, w2, start, step);
+      matvec_reg<T, P>(out, Mx, v);
+      load_line<T, P>(r1, w1, start, step);
+      T* yo = y + cbase + (long long)e * P3 + start;
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        out[a] += r1[a];
+        if (do_scale) out[a] *= scale;
+        yo[a] = out[a];
+      }
+    }
+  }
 }
 
 // y = M^-1 x = (Mx^-1 x My^-1 x Mz^-1) x cell by cell (Sec. 5: tensorial inverse

@@ -12,7 +12,29 @@ template <typename T, int P>
 static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu, const T* nu_cell, bool stiff,
                           const DotSink* sink, int* nblocks, cudaStream_t s) {
   const int prec = sizeof(T) == 8 ? 0 : 1;
-  const int cpb = m.cpb[prec] > 0 ? m.cpb[prec] : default_cpb(P, prec);
+  const bool uniform_ = stiff && nu_cell == nullptr;
+  if constexpr (std::is_same<T, float>::value) {
+    if (uniform_ && m.f32_mapping == 1 && (!sink || !sink->partials)) {
+      // FP32 plane mapping: P threads per cell
+      const int cpbp = cells_per_block(m, 1);
+      const int thr = (cpbp * P + 31) / 32 * 32;
+      const size_t smp = (size_t)3 * cpbp * P * P * P * sizeof(float);
+      if (thr > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
+      if (smp + 2048 > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(apply_plane_kernel<float, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smp);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply plane)");
+      }
+      const dim3 gridp((unsigned)((m.ncell + cpbp - 1) / cpbp), (unsigned)ncomp);
+      apply_plane_kernel<float, P><<<gridp, thr, smp, s>>>(make_geo<float>(m), x, y, cpbp, cm / nu, nu,
+                                                           nu != 1.f ? 1 : 0, cm != 0.f ? 1 : 0);
+      if (nblocks) *nblocks = (int)(gridp.x * gridp.y);
+      const_cast<Mesh&>(m).launches++;
+      cudaError_t e = cudaGetLastError();
+      return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch");
+    }
+  }
+  const int cpb = m.f32_mapping == 1 && prec == 1 ? default_cpb(P, prec) : cells_per_block(m, prec);
   const Geo<T> g = make_geo<T>(m);
   const dim3 grid((unsigned)((m.ncell + cpb - 1) / cpb), (unsigned)ncomp);
   const int threads = (cpb * P * P + 31) / 32 * 32;  // whole warps (the block reduction shuffles full warps)

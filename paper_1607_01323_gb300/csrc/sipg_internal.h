@@ -73,6 +73,7 @@ struct Mesh {
   float* dtab32[3] = {nullptr, nullptr, nullptr};
   dfl* dtabdf[3] = {nullptr, nullptr, nullptr};  // double-float copies (hi, lo)
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
+  int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
   // profiling
   bool profile = false;
@@ -151,5 +152,7 @@ void prof_begin(Mesh& m, cudaStream_t s, cudaEvent_t* e0);
 void prof_end(Mesh& m, cudaStream_t s, cudaEvent_t e0);
 
 int default_cpb(int p, int precision);
+int default_cpb_plane(int p);
+int cells_per_block(const Mesh& m, int precision);  // current setting or default for the mapping
 
 }  // namespace sipg

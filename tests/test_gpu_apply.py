@@ -136,11 +136,13 @@ def test_laplace_ragged_tiles(cpb):
     assert scaled_err(y32, A @ x32.astype(np.float64), norm_a, x) <= TOL32
 
 
-@pytest.mark.parametrize("name,c,k,pen", CASES[:1] + CASES[3:10], ids=[x[0] for x in CASES[:1] + CASES[3:10]])
-def test_laplace_f32_parity(name, c, k, pen):
+@pytest.mark.parametrize("mapping", ["plane", "line"])
+@pytest.mark.parametrize("name,c,k,pen", CASES[:1] + CASES[2:10], ids=[x[0] for x in CASES[:1] + CASES[2:10]])
+def test_laplace_f32_parity(name, c, k, pen, mapping):
     from paper_1607_01323_gb300 import apply_laplace_f32
     op = SIPG(oracle_spec(c), k, penalty_factor=pen)
     m = gpu_mesh(c, k, penalty=pen)
+    m.set_f32_mapping(mapping)
     x = uniform(m.n_dofs, "x").astype(np.float32)
     A = op.assemble()
     y = apply_laplace_f32(m, _cuda(x, torch.float32)).cpu().numpy().astype(np.float64)
@@ -161,8 +163,10 @@ def test_helmholtz_f64_parity(k):
     y = apply_helmholtz_f64(m, _cuda(x), cm, nu).cpu().numpy()
     norm_a = abs(A).sum(axis=1).max()
     assert scaled_err(y, y_ref, norm_a, x) <= TOL64
-    y32 = apply_helmholtz_f32(m, _cuda(x, torch.float32), cm, nu).cpu().numpy()
-    assert scaled_err(y32, y_ref, norm_a, x) <= TOL32
+    for mapping in ("plane", "line"):
+        m.set_f32_mapping(mapping)
+        y32 = apply_helmholtz_f32(m, _cuda(x, torch.float32), cm, nu).cpu().numpy()
+        assert scaled_err(y32, y_ref, norm_a, x) <= TOL32
     # per-cell viscosity nu_e = exp(0.5 xi_e) / 180
     nu_cell = np.exp(0.5 * inputs.normal(0, "xi", m.ncell)) / 180.0
     A = op.assemble(mass_coef=cm, nu_cell=nu_cell)
