@@ -29,7 +29,7 @@ class MeshSpec:
     hi: tuple = (1.0, 1.0, 1.0)
     bc_lo: tuple = (PERIODIC, PERIODIC, PERIODIC)
     bc_hi: tuple = (PERIODIC, PERIODIC, PERIODIC)
-    mapping: str = "affine"  # "affine" or "channel"
+    mapping: str = "affine"  # "affine", "channel", or "channel_linear"
     gamma: float = 1.8
     n: tuple = field(init=False)
 
@@ -53,6 +53,15 @@ def analytic_map(spec, s):
     if spec.mapping == "channel":
         g = spec.gamma
         t = np.tanh(g * (2.0 * s[..., 1] - 1.0)) / np.tanh(g)
+        x[..., 1] = lo[1] + (hi[1] - lo[1]) * 0.5 * (1.0 + t)
+    elif spec.mapping == "channel_linear":
+        # the tanh grading at the cell boundaries eta_j = j / ny, linear in between
+        g, ny = spec.gamma, spec.ny
+        j = np.clip(np.floor(s[..., 1] * ny), 0, ny - 1)
+        e0, e1 = j / ny, (j + 1) / ny
+        y0 = np.tanh(g * (2.0 * e0 - 1.0)) / np.tanh(g)
+        y1 = np.tanh(g * (2.0 * e1 - 1.0)) / np.tanh(g)
+        t = y0 + (y1 - y0) * (s[..., 1] - e0) * ny
         x[..., 1] = lo[1] + (hi[1] - lo[1]) * 0.5 * (1.0 + t)
     elif spec.mapping != "affine":
         raise ValueError("unknown mapping " + spec.mapping)

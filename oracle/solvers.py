@@ -117,3 +117,30 @@ def chebyshev(apply, diag, b, degree, lmin, lmax):
         d = rho_new * rho * d + (2.0 * rho_new / delta) * (r / diag)
         rho = rho_new
     return x
+
+
+def chebyshev_from(apply, diag, b, x0, degree, lmin, lmax):
+    """``degree`` Chebyshev steps for A x = b preconditioned by D = diag(A),
+    from the initial guess x0 (None: zero; then the first step needs no
+    operator product).  Same recurrence as ``chebyshev``; with x0 the first
+    residual is b - A x0."""
+    theta = 0.5 * (lmax + lmin)
+    delta = 0.5 * (lmax - lmin)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    if x0 is None:
+        x = np.zeros_like(b)
+        r = b.copy()
+    else:
+        x = np.array(x0, dtype=np.float64)
+        r = b - apply(x)
+    d = (r / diag) / theta
+    for step in range(degree):
+        x = x + d
+        if step == degree - 1:
+            break
+        r = r - apply(d)
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * (r / diag)
+        rho = rho_new
+    return x
