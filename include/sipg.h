@@ -58,14 +58,15 @@ typedef enum {
 } sipg_status;
 
 typedef enum { SIPG_BC_PERIODIC = 0, SIPG_BC_DIRICHLET = 1, SIPG_BC_NEUMANN = 2 } sipg_bc;
-typedef enum { SIPG_MAP_AFFINE = 0, SIPG_MAP_CHANNEL_TANH = 1 } sipg_map;
+typedef enum { SIPG_MAP_AFFINE = 0, SIPG_MAP_CHANNEL_TANH = 1, SIPG_MAP_CHANNEL_LINEAR = 2 } sipg_map;
 typedef enum { SIPG_OP_LAPLACE = 0, SIPG_OP_HELMHOLTZ = 1 } sipg_op;
 typedef enum { SIPG_F64_NATIVE = 0, SIPG_F64_DOUBLE_FLOAT = 1 } sipg_f64_arith;
 typedef enum {
   SIPG_PC_NONE = 0,
   SIPG_PC_JACOBI = 1,     /* z = diag(A)^-1 r (Sec. 5.1: the diagonal computed once)   */
   SIPG_PC_INVMASS = 2,    /* z = M^-1 r (Sec. 5.1: viscous solver preconditioner)       */
-  SIPG_PC_CHEB_F32 = 3    /* Chebyshev in FP32 with the FP32 operator (Sec. 5.1)         */
+  SIPG_PC_CHEB_F32 = 3,   /* Chebyshev in FP32 with the FP32 operator (Sec. 5.1)         */
+  SIPG_PC_GMG_F32 = 4     /* one geometric-multigrid V-cycle in FP32 (Sec. 5.1)         */
 } sipg_precond;
 
 /* Mesh description.  "Dirichlet" is the side where the unknown is prescribed
@@ -75,7 +76,10 @@ typedef enum {
  * treated as interior faces.  map = SIPG_MAP_CHANNEL_TANH maps the global
  * wall-normal coordinate eta in [0,1] to
  *   y = lo[1] + (hi[1]-lo[1]) (1 + tanh(gamma (2 eta - 1)) / tanh(gamma)) / 2
- * (Sec. 7.1 with delta = 1 for lo=-1, hi=1); x and z stay affine. */
+ * (Sec. 7.1 with delta = 1 for lo=-1, hi=1); x and z stay affine.
+ * map = SIPG_MAP_CHANNEL_LINEAR takes the same y at the cell boundaries
+ * eta_j = j / n[1] and is affine inside each cell (straight cells on the
+ * graded vertices; the coarse levels of the multigrid hierarchy). */
 typedef struct {
   int n[3];          /* cells per direction, each >= 1                         */
   double lo[3];      /* box corner                                             */
@@ -164,11 +168,17 @@ typedef struct {
   int flexible;           /* Polak-Ribiere beta (always used with SIPG_PC_CHEB_F32)         */
   int use_graph;          /* capture check_every iterations in one CUDA graph and replay it  */
   int check_every;        /* iterations between host convergence checks (>= 1)             */
+  /* SIPG_PC_GMG_F32 (Laplace, one component): */
+  int mg_degree;          /* Chebyshev smoother steps before and after the coarse correction */
+  double mg_range;        /* smoothing range: [lambda_max / mg_range, lambda_max] per level   */
+  double mg_coarse_tol;   /* coarse Chebyshev: degree where the error estimate reaches this   */
+  int mg_coarse_maxdeg;   /* upper bound on that degree                                       */
 } sipg_cg_opts;
 
 /* Fill opts with defaults: Laplace, Jacobi, rtol 1e-10, maxit 10000, Chebyshev
  * degree 4, range 20, estimated lambda_max with 20 steps, graph on, checks
- * every 16 iterations. */
+ * every 16 iterations; multigrid smoother degree 5, range 20, coarse
+ * tolerance 1e-3 (Sec. 5.1), coarse degree at most 200. */
 int sipg_cg_default_opts(sipg_cg_opts* opts);
 
 /* Solve A x = b by preconditioned CG (Sec. 5.1) with the matrix-free FP64
@@ -212,6 +222,49 @@ int sipg_cg_solve(sipg_mesh* mesh, const sipg_cg_opts* opts, const double* b, do
  * the caller.  Returns the same statuses as sipg_cg_solve. */
 int sipg_cg_solve_noalloc(sipg_mesh* mesh, const sipg_cg_opts* opts, const double* b, double* x, int ncomp,
                           void* stream, int* iters_out, double* relres_out);
+
+/* Geometric multigrid (Sec. 5.1), the preconditioner SIPG_PC_GMG_F32.
+ *
+ * Levels: the mesh, then the mesh with half the cells in every direction whose
+ * count is even and > 1, and so on down to the level where no direction can be
+ * halved (one cell for power-of-two meshes).  Every level keeps the degree,
+ * penalty factor and boundary conditions and re-discretises the SIPG Laplacian
+ * on its own geometry tables; on the coarse levels of a tanh channel each cell
+ * is straight between the graded vertices (SIPG_MAP_CHANNEL_LINEAR).
+ * One V-cycle, entirely in FP32 with the FP32 operator: on each level
+ * mg_degree Chebyshev steps on D^-1 A from zero (D = diag(A) of the level,
+ * interval [lambda_max / mg_range, lambda_max]), the residual restricted to the
+ * next level, the coarse correction prolongated and added, and mg_degree
+ * Chebyshev steps from that iterate; on the coarsest level a Chebyshev
+ * iteration from zero on [lambda_min, lambda_max] whose degree is the smallest
+ * with 2 s^d / (1 + s^2d) <= mg_coarse_tol, s = (sqrt(kappa) - 1) / (sqrt(kappa) + 1).
+ * Prolongation evaluates the parent cell's polynomial at the child's nodes
+ * (tensorial embedding); restriction is its transpose.  The eigenvalue
+ * estimates come from cheb_lanczos_steps Jacobi-PCG steps on each level
+ * (Lanczos), lambda_max with a factor 1.1; on the coarsest level up to 120
+ * steps give lambda_min (factor 0.9) and lambda_max (factor 1.1).  No
+ * zero-mean projection inside the cycle (Sec. 5.1).
+ *
+ * sipg_mg_setup builds the levels and the estimates for the options' mg_*
+ * fields and cheb_lanczos_steps (op must be SIPG_OP_LAPLACE); the result is
+ * cached on the mesh and reused by every later sipg_cg_solve with
+ * SIPG_PC_GMG_F32 and the same options (sipg_cg_solve sets it up on first use;
+ * sipg_set_degree and sipg_set_penalty drop it).  Synchronous.  Device memory:
+ * six FP32 vectors per level plus two FP64 vectors of the finest size. */
+int sipg_mg_setup(sipg_mesh* mesh, const sipg_cg_opts* opts, void* stream);
+
+/* The hierarchy built by sipg_mg_setup (HOST outputs, arrays of max_levels
+ * entries, NULL allowed): number of levels, cells per direction of each level
+ * (n_cells[3 * l + d]), the lambda_max used on each level (for the coarsest,
+ * the upper end of its interval), the coarse interval's lower end and the
+ * coarse Chebyshev degree.  EINVAL if no hierarchy is set up. */
+int sipg_mg_info(const sipg_mesh* mesh, int max_levels, int* nlevels, int* n_cells, double* lmax,
+                 double* coarse_lmin, int* coarse_degree);
+
+/* z = V(r): one V-cycle of the hierarchy set up on the mesh, applied to the
+ * FP64 vector r (DEVICE, n_dofs doubles; rounded to FP32), result z (DEVICE,
+ * n_dofs doubles).  Asynchronous on `stream`. */
+int sipg_mg_vcycle(sipg_mesh* mesh, const double* r, double* z, void* stream);
 
 /* Size in bytes of the static workspace of sipg_cg_solve_noalloc (host output). */
 int sipg_cg_noalloc_capacity(long long* bytes);

@@ -16,7 +16,7 @@ from . import _lib as L
 
 __all__ = ["Mesh", "create_mesh", "apply_laplace_f64", "apply_laplace_f32", "apply_helmholtz_f64",
            "apply_helmholtz_f32", "apply_mass_f64", "apply_inverse_mass_f64", "diagonal_f64", "cg_solve",
-           "adjoint_grad_nu", "autotune", "CgResult", "SipgError"]
+           "mg_setup", "mg_info", "mg_vcycle", "adjoint_grad_nu", "autotune", "CgResult", "SipgError"]
 
 SipgError = L.SipgError
 
@@ -47,8 +47,9 @@ class Mesh:
     """A structured hexahedral mesh with its geometry tables on the current GPU.
 
     n: cells per direction; lo, hi: box; bc_lo / bc_hi: 'periodic',
-    'dirichlet' or 'neumann' per direction; mapping: 'affine' or 'channel'
-    (tanh grading of y with parameter gamma); k: polynomial degree;
+    'dirichlet' or 'neumann' per direction; mapping: 'affine', 'channel'
+    (tanh grading of y with parameter gamma) or 'channel_linear' (the graded
+    cell vertices with straight cells); k: polynomial degree;
     penalty: factor on tau of Eq. (taue)."""
 
     def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc_lo=("periodic",) * 3,
@@ -261,6 +262,34 @@ def cg_solve(mesh, b, x=None, stream=None, raise_on_fail=True, **opts):
     if raise_on_fail:
         L.check(st)
     return x, CgResult(st, it.value, rel.value)
+
+
+def mg_setup(mesh, stream=None, **opts):
+    """Build (or reuse) the multigrid hierarchy for the given sipg_cg_opts fields."""
+    o = cg_opts(**opts)
+    L.check(L.lib().sipg_mg_setup(mesh.handle, C.byref(o), _stream_ptr(stream)))
+    return mg_info(mesh)
+
+
+def mg_info(mesh, max_levels=32):
+    """dict(nlevels, n_cells [list of (nx, ny, nz)], lmax [per level], coarse_lmin, coarse_degree)."""
+    nl, cdeg, clmin = C.c_int(), C.c_int(), C.c_double()
+    cells = (C.c_int * (3 * max_levels))()
+    lmax = (C.c_double * max_levels)()
+    L.check(L.lib().sipg_mg_info(mesh.handle, max_levels, C.byref(nl), cells, lmax, C.byref(clmin), C.byref(cdeg)))
+    n = min(nl.value, max_levels)
+    return dict(nlevels=nl.value, n_cells=[tuple(cells[3 * i:3 * i + 3]) for i in range(n)],
+                lmax=[lmax[i] for i in range(n)], coarse_lmin=clmin.value, coarse_degree=cdeg.value)
+
+
+def mg_vcycle(mesh, r, z=None, stream=None):
+    """z = V(r), one FP32 V-cycle of the hierarchy set up by mg_setup."""
+    torch = _torch()
+    if z is None:
+        z = torch.empty_like(r)
+    L.check(L.lib().sipg_mg_vcycle(mesh.handle, _dev(r, torch.float64, "r"), _dev(z, torch.float64, "z"),
+                                   _stream_ptr(stream)))
+    return z
 
 
 def adjoint_grad_nu(mesh, nu_cell, u, lam, out=None, stream=None):

@@ -7,9 +7,9 @@ LIB_PATH = os.path.join(HERE, "libsipg.so")
 
 OK, MAXITER, EINVAL, ECUDA, ENOMEM, BREAKDOWN, NONFINITE = 0, 1, -1, -2, -3, -4, -5
 BC = {"periodic": 0, "dirichlet": 1, "neumann": 2}
-MAP = {"affine": 0, "channel": 1}
+MAP = {"affine": 0, "channel": 1, "channel_linear": 2}
 OP = {"laplace": 0, "helmholtz": 1}
-PC = {"none": 0, "jacobi": 1, "invmass": 2, "cheb_f32": 3}
+PC = {"none": 0, "jacobi": 1, "invmass": 2, "cheb_f32": 3, "gmg_f32": 4}
 
 
 class MeshDesc(C.Structure):
@@ -22,7 +22,8 @@ class CgOpts(C.Structure):
                 ("precond", C.c_int), ("cheb_degree", C.c_int), ("cheb_range", C.c_double),
                 ("cheb_lmax", C.c_double), ("cheb_lanczos_steps", C.c_int), ("zero_mean", C.c_int),
                 ("rtol", C.c_double), ("maxit", C.c_int), ("flexible", C.c_int), ("use_graph", C.c_int),
-                ("check_every", C.c_int)]
+                ("check_every", C.c_int), ("mg_degree", C.c_int), ("mg_range", C.c_double),
+                ("mg_coarse_tol", C.c_double), ("mg_coarse_maxdeg", C.c_int)]
 
 
 class SipgError(RuntimeError):
@@ -58,6 +59,10 @@ _SIGS = {
     "sipg_cg_solve_noalloc": [C.c_void_p, C.POINTER(CgOpts), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                               C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "sipg_cg_noalloc_capacity": [C.POINTER(C.c_longlong)],
+    "sipg_mg_setup": [C.c_void_p, C.POINTER(CgOpts), C.c_void_p],
+    "sipg_mg_info": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                     C.POINTER(C.c_int)],
+    "sipg_mg_vcycle": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_adjoint_grad_nu": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_autotune": [C.c_void_p, C.c_int, C.c_char_p],
     "sipg_set_f64_arithmetic": [C.c_void_p, C.c_int],

@@ -29,6 +29,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 }
 
 Mesh::~Mesh() {
+  mg_release(*this);
   for (int d = 0; d < 3; ++d) {
     if (dtab64[d]) cudaFree(dtab64[d]);
     if (dtab32[d]) cudaFree(dtab32[d]);
@@ -181,8 +182,9 @@ int sipg_create_mesh(const sipg_mesh_desc* d, sipg_mesh** out) {
     if ((d->bc_lo[i] == SIPG_BC_PERIODIC) != (d->bc_hi[i] == SIPG_BC_PERIODIC))
       return fail(SIPG_EINVAL, "periodic sides must be paired");
   }
-  if (d->map != SIPG_MAP_AFFINE && d->map != SIPG_MAP_CHANNEL_TANH) return fail(SIPG_EINVAL, "unknown map");
-  if (d->map == SIPG_MAP_CHANNEL_TANH && !(d->gamma > 0.0 && std::isfinite(d->gamma)))
+  if (d->map != SIPG_MAP_AFFINE && d->map != SIPG_MAP_CHANNEL_TANH && d->map != SIPG_MAP_CHANNEL_LINEAR)
+    return fail(SIPG_EINVAL, "unknown map");
+  if (d->map != SIPG_MAP_AFFINE && !(d->gamma > 0.0 && std::isfinite(d->gamma)))
     return fail(SIPG_EINVAL, "channel map needs gamma > 0");
   long long nc = (long long)d->n[0] * d->n[1] * d->n[2];
   if (nc * 512 >= (1LL << 31) * 8LL) return fail(SIPG_EINVAL, "mesh too large");
@@ -221,6 +223,7 @@ int sipg_set_degree(sipg_mesh* m, int k) {
   if (k < 1 || k > 7) return fail(SIPG_EINVAL, "degree must be 1 <= k <= 7");
   if ((st = set_device(*m))) return st;
   cudaDeviceSynchronize();
+  mg_release(*m);
   const int k0 = m->k;
   m->k = k;
   m->p = k + 1;
@@ -241,6 +244,7 @@ int sipg_set_penalty(sipg_mesh* m, double f) {
   if (!(f > 0.0) || !std::isfinite(f)) return fail(SIPG_EINVAL, "penalty factor must be > 0");
   if ((st = set_device(*m))) return st;
   cudaDeviceSynchronize();  // the tables hold the penalty shares: no launch may still read them
+  mg_release(*m);
   const double f0 = m->penalty;
   m->penalty = f;
   st = build_tables(*m);
@@ -373,6 +377,10 @@ int sipg_cg_default_opts(sipg_cg_opts* o) {
   o->flexible = 0;
   o->use_graph = 1;
   o->check_every = 16;
+  o->mg_degree = 5;
+  o->mg_range = 20.0;
+  o->mg_coarse_tol = 1e-3;
+  o->mg_coarse_maxdeg = 200;
   return SIPG_OK;
 }
 
@@ -385,7 +393,11 @@ int sipg_cg_solve(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* 
   if (o->op != SIPG_OP_LAPLACE && o->op != SIPG_OP_HELMHOLTZ) return fail(SIPG_EINVAL, "unknown operator");
   if (o->op == SIPG_OP_HELMHOLTZ && (!(o->mass_coef >= 0.0) || (!o->nu_cell && !(o->nu > 0.0))))
     return fail(SIPG_EINVAL, "Helmholtz needs mass_coef >= 0 and nu > 0");
-  if (o->precond < SIPG_PC_NONE || o->precond > SIPG_PC_CHEB_F32) return fail(SIPG_EINVAL, "unknown preconditioner");
+  if (o->precond < SIPG_PC_NONE || o->precond > SIPG_PC_GMG_F32) return fail(SIPG_EINVAL, "unknown preconditioner");
+  if (o->precond == SIPG_PC_GMG_F32) {
+    if (o->op != SIPG_OP_LAPLACE) return fail(SIPG_EINVAL, "the multigrid preconditioner supports the Laplace operator");
+    if (ncomp != 1) return fail(SIPG_EINVAL, "the multigrid preconditioner supports one component");
+  }
   if (o->precond == SIPG_PC_CHEB_F32) {
     if (o->cheb_degree < 1 || o->cheb_degree > 64) return fail(SIPG_EINVAL, "cheb_degree must be in [1, 64]");
     if (!(o->cheb_range > 1.0)) return fail(SIPG_EINVAL, "cheb_range must be > 1");
@@ -445,6 +457,37 @@ int sipg_cg_solve_noalloc(sipg_mesh* m, const sipg_cg_opts* o, const double* b, 
     return fail(SIPG_EINVAL, "singular Laplace problem (no Dirichlet side): set zero_mean");
   if ((st = set_device(*m))) return st;
   return cg_solve_noalloc(*m, *o, b, x, ncomp, (cudaStream_t)stream, iters, relres);
+}
+
+int sipg_mg_setup(sipg_mesh* m, const sipg_cg_opts* o, void* stream) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!o) return fail(SIPG_EINVAL, "opts is NULL");
+  bool all_bc_free = true;
+  for (int d = 0; d < 3; ++d)
+    if (m->desc.bc_lo[d] == SIPG_BC_DIRICHLET || m->desc.bc_hi[d] == SIPG_BC_DIRICHLET) all_bc_free = false;
+  if (all_bc_free && !o->zero_mean)
+    return fail(SIPG_EINVAL, "singular Laplace problem (no Dirichlet side): set zero_mean");
+  if ((st = set_device(*m))) return st;
+  return mg_setup(*m, *o, (cudaStream_t)stream);
+}
+
+int sipg_mg_info(const sipg_mesh* m, int max_levels, int* nlevels, int* n_cells, double* lmax, double* coarse_lmin,
+                 int* coarse_degree) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (max_levels < 0) return fail(SIPG_EINVAL, "max_levels must be >= 0");
+  return mg_info(*m, max_levels, nlevels, n_cells, lmax, coarse_lmin, coarse_degree);
+}
+
+int sipg_mg_vcycle(sipg_mesh* m, const double* r, double* z, void* stream) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!r || !z) return fail(SIPG_EINVAL, "NULL vector");
+  if (r == z) return fail(SIPG_EINVAL, "r and z must not overlap");
+  if (!m->mg) return fail(SIPG_EINVAL, "no multigrid hierarchy set up on this mesh (sipg_mg_setup)");
+  if ((st = set_device(*m))) return st;
+  return mg_vcycle(*m, r, z, nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 int sipg_cg_noalloc_capacity(long long* bytes) {

@@ -995,16 +995,22 @@ __global__ void diagonal_kernel(Geo<double> g, int stiffness, double mass_coef, 
     md[dir] = c.L[O::M + a * P + a];
     double k = nue * c.L[O::K + a * P + a];
     if (a == P - 1) {
-      if (c.kindR == 0)
+      if (c.kindR == 0) {
         k += -nue * c.L[O::dR + P - 1] + c.tauFR * (nue > c.nuR ? nue : c.nuR);
-      else if (c.kindR == SIPG_BC_DIRICHLET)
+        // one cell across a periodic direction: the "neighbour" trace is this
+        // node's own left-end derivative (self-coupling on the diagonal)
+        if (c.nbR == e) k += -nue * c.L[O::dL + P - 1];
+      } else if (c.kindR == SIPG_BC_DIRICHLET) {
         k += -2.0 * nue * c.L[O::dR + P - 1] + 2.0 * tau_e * nue;
+      }
     }
     if (a == 0) {
-      if (c.kindL == 0)
+      if (c.kindL == 0) {
         k += nue * c.L[O::dL] + c.tauFL * (nue > c.nuL ? nue : c.nuL);
-      else if (c.kindL == SIPG_BC_DIRICHLET)
+        if (c.nbL == e) k += nue * c.L[O::dR];
+      } else if (c.kindL == SIPG_BC_DIRICHLET) {
         k += 2.0 * nue * c.L[O::dL] + 2.0 * tau_e * nue;
+      }
     }
     kd[dir] = k;
   }

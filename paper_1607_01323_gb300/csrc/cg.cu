@@ -16,7 +16,9 @@
 // (Sec. 5.1: the preconditioner runs in single precision under an FP64 outer
 // CG; the eigenvalue bound comes from an initial CG run).  With the FP32
 // Chebyshev preconditioner the outer CG uses the flexible (Polak-Ribiere)
-// beta, since rounding makes the preconditioner slightly non-linear.
+// beta, since rounding makes the preconditioner slightly non-linear.  The
+// geometric-multigrid V-cycle (mg.cu, Sec. 5.1) is a separate preconditioner of
+// the same kind (FP32, flexible beta).
 // Singular problems (zero_mean): b and every operator product are projected
 // onto vectors with zero mean (Sec. 5.1).
 #include <cmath>
@@ -683,7 +685,10 @@ struct Solver {
     return SIPG_OK;
   }
 
-  bool separate_precond() const { return o.precond == SIPG_PC_INVMASS || o.precond == SIPG_PC_CHEB_F32; }
+  bool separate_precond() const {
+    return o.precond == SIPG_PC_INVMASS || o.precond == SIPG_PC_CHEB_F32 || o.precond == SIPG_PC_GMG_F32;
+  }
+  bool fp32_precond() const { return o.precond == SIPG_PC_CHEB_F32 || o.precond == SIPG_PC_GMG_F32; }
 
   // one CG iteration (no host synchronisation)
   int iteration() {
@@ -692,7 +697,7 @@ struct Solver {
     const bool sep = separate_precond();
     const double* dg = o.precond == SIPG_PC_JACOBI ? w.diag : nullptr;
     double* z = (o.precond == SIPG_PC_NONE) ? w.r : w.z;
-    const int flex = o.precond == SIPG_PC_CHEB_F32 || (o.flexible && o.precond != SIPG_PC_INVMASS);
+    const int flex = fp32_precond() || (o.flexible && o.precond != SIPG_PC_INVMASS);
     pick_update(!sep, o.zero_mean != 0, flex != 0)<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, xcur, w.r, w.p, w.ap,
                                                                                       z, dg, w.part1, flex);
     if ((st = launched())) return st;
@@ -704,6 +709,8 @@ struct Solver {
                   ncomp);
     } else if (o.precond == SIPG_PC_CHEB_F32) {
       if ((st = cheb_apply(w.z, w.r, w.ap, w.sc))) return st;
+    } else if (o.precond == SIPG_PC_GMG_F32) {
+      if ((st = mg_vcycle(m, w.r, w.z, w.ap, &w.sc->done, &w.sc->mean, w.part2, s))) return st;
     }
     // with a separate preconditioner, beta and the convergence test need its
     // partials: one reduction kernel (the Jacobi / none path did them in k_update)
@@ -760,6 +767,8 @@ struct Solver {
         if ((st = launch_inverse_mass(m, w.r, w.z, ncomp, w.part2, nullptr, s))) return st;
         const int cpb = m.cpb[0] > 0 ? m.cpb[0] : default_cpb(m.p, 0);
         nb2 = (int)(((m.ncell + cpb - 1) / cpb) * ncomp);
+      } else if (o.precond == SIPG_PC_GMG_F32) {
+        if ((st = mg_vcycle(m, w.r, w.z, nullptr, nullptr, nullptr, w.part2, s))) return st;
       } else {
         if ((st = cheb_apply(w.z, w.r, nullptr, nullptr))) return st;
       }
@@ -836,14 +845,76 @@ struct Solver {
 
 }  // namespace
 
+int lanczos_extremes(Mesh& lm, const sipg_cg_opts& o, const double* b, int ncomp, int steps, double rtol,
+                     cudaStream_t s, double* ritz_min, double* ritz_max) {
+  const long long N = lm.ncell * lm.p * lm.p * lm.p;
+  const long long n = N * ncomp;
+  const int cpb0 = lm.cpb[0] > 0 ? lm.cpb[0] : default_cpb(lm.p, 0);
+  const int nb_apply = (int)(((lm.ncell + cpb0 - 1) / cpb0) * ncomp);
+  Workspace w;
+  int st = ensure_ws(lm, n, nb_apply, false, w);
+  if (st) return st;
+  const bool helm = o.op == SIPG_OP_HELMHOLTZ;
+  const double cm = helm ? o.mass_coef : 0.0, nu = helm ? o.nu : 1.0;
+  const double* nuc = helm ? o.nu_cell : nullptr;
+  sipg_cg_opts lo = o;
+  lo.precond = SIPG_PC_JACOBI;
+  lo.flexible = 0;
+  lo.use_graph = 0;
+  lo.check_every = steps;
+  Solver L(lm, lo, ncomp, s);
+  L.w = w;
+  if ((st = launch_diagonal(lm, true, cm, nu, nuc, w.xs, s))) return st;
+  k_inv_rep<<<kVecBlocks, kVecThreads, 0, s>>>(n, N, w.xs, w.diag);
+  if ((st = L.launched())) return st;
+  k_fill<<<kVecBlocks, kVecThreads, 0, s>>>(n, 0.0, w.xs);
+  if ((st = L.launched())) return st;
+  steps = steps < kMaxLanczos ? steps : kMaxLanczos;
+  int it = 0, done = 0;
+  double rel = 0;
+  if ((st = L.run(b, w.xs, steps, rtol, true, &it, &rel, &done))) return st;
+  if (done == NONFINITE || done == BREAKDOWN) return fail(SIPG_NONFINITE, "eigenvalue estimate: CG broke down");
+  std::vector<double> la(kMaxLanczos), lb(kMaxLanczos);
+  const char* scb = reinterpret_cast<const char*>(w.sc);
+  cudaError_t e = cudaMemcpy(la.data(), scb + offsetof(Scalars, lan_alpha), sizeof(double) * kMaxLanczos,
+                             cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(lb.data(), scb + offsetof(Scalars, lan_beta), sizeof(double) * kMaxLanczos, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read Lanczos data");
+  const int mm = it < kMaxLanczos ? it : kMaxLanczos;
+  if (mm < 1) return fail(SIPG_EINVAL, "eigenvalue estimate needs at least one CG step");
+  // Lanczos tridiagonal from the CG coefficients (Saad, Sec. 6.7.3)
+  std::vector<double> a(mm), off(mm > 1 ? mm - 1 : 0), an(mm), offn(off.size());
+  for (int i = 0; i < mm; ++i) {
+    a[i] = 1.0 / la[i] + (i > 0 ? lb[i - 1] / la[i - 1] : 0.0);
+    if (i + 1 < mm) off[i] = std::sqrt(lb[i]) / la[i];
+  }
+  for (int i = 0; i < mm; ++i) an[i] = -a[i];
+  for (size_t i = 0; i < off.size(); ++i) offn[i] = -off[i];
+  if (ritz_max) *ritz_max = tridiag_max_eig(a, off);
+  if (ritz_min) *ritz_min = -tridiag_max_eig(an, offn);
+  return SIPG_OK;
+}
+
 int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s, int* iters,
              double* relres) {
   const long long N = m.ncell * m.p * m.p * m.p;
   const long long n = N * ncomp;
   const int cpb0 = m.cpb[0] > 0 ? m.cpb[0] : default_cpb(m.p, 0);
   const int nb_apply = (int)(((m.ncell + cpb0 - 1) / cpb0) * ncomp);
+  int st;
+  // the multigrid set-up runs its own CG on the mesh's workspace: before this solve's
+  if (o.precond == SIPG_PC_GMG_F32 && (st = mg_setup(m, o, s))) return st;
+  double lmax = o.cheb_lmax;
+  if (o.precond == SIPG_PC_CHEB_F32 && !(lmax > 0.0)) {
+    // lambda_max of D^-1 A from a short Jacobi-PCG run on A y = b (Lanczos from
+    // the CG coefficients), as the paper estimates the Chebyshev interval.
+    double rmin = 0.0;
+    if ((st = lanczos_extremes(m, o, b, ncomp, o.cheb_lanczos_steps, 0.0, s, &rmin, &lmax))) return st;
+    lmax *= 1.1;  // safety factor 1.1 on the estimate
+  }
   Workspace w;
-  int st = ensure_ws(m, n, nb_apply, o.precond == SIPG_PC_CHEB_F32, w);
+  st = ensure_ws(m, n, nb_apply, o.precond == SIPG_PC_CHEB_F32, w);
   if (st) return st;
   Solver S(m, o, ncomp, s);
   S.w = w;
@@ -858,41 +929,6 @@ int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int nco
   if (o.precond == SIPG_PC_CHEB_F32) {
     k_inv_f32<<<kVecBlocks, kVecThreads, 0, s>>>(n, w.diag, w.dinv32);
     if ((st = S.launched())) return st;
-    double lmax = o.cheb_lmax;
-    if (!(lmax > 0.0)) {
-      // lambda_max of D^-1 A from a short Jacobi-PCG run on A y = b (Lanczos from
-      // the CG coefficients), as the paper estimates the Chebyshev interval.
-      sipg_cg_opts lo = o;
-      lo.precond = SIPG_PC_JACOBI;
-      lo.flexible = 0;
-      lo.use_graph = 0;
-      lo.check_every = o.cheb_lanczos_steps;
-      Solver L(m, lo, ncomp, s);
-      L.w = w;
-      k_fill<<<kVecBlocks, kVecThreads, 0, s>>>(n, 0.0, w.xs);
-      if ((st = S.launched())) return st;
-      int it = 0, done = 0;
-      double rel = 0;
-      const int steps = o.cheb_lanczos_steps < kMaxLanczos ? o.cheb_lanczos_steps : kMaxLanczos;
-      if ((st = L.run(b, w.xs, steps, 0.0, true, &it, &rel, &done))) return st;
-      if (done == NONFINITE) return fail(SIPG_NONFINITE, "non-finite values in the eigenvalue estimate");
-      std::vector<double> la(kMaxLanczos), lb(kMaxLanczos);
-      const char* scb = reinterpret_cast<const char*>(w.sc);
-      cudaError_t e = cudaMemcpy(la.data(), scb + offsetof(Scalars, lan_alpha), sizeof(double) * kMaxLanczos,
-                                 cudaMemcpyDeviceToHost);
-      if (e == cudaSuccess)
-        e = cudaMemcpy(lb.data(), scb + offsetof(Scalars, lan_beta), sizeof(double) * kMaxLanczos,
-                       cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) return cuda_fail(e, "read Lanczos data");
-      const int mm = it < kMaxLanczos ? it : kMaxLanczos;
-      if (mm < 1) return fail(SIPG_EINVAL, "eigenvalue estimate needs at least one CG step");
-      std::vector<double> a(mm), off(mm > 1 ? mm - 1 : 0);
-      for (int i = 0; i < mm; ++i) {
-        a[i] = 1.0 / la[i] + (i > 0 ? lb[i - 1] / la[i - 1] : 0.0);
-        if (i + 1 < mm) off[i] = std::sqrt(lb[i]) / la[i];
-      }
-      lmax = 1.1 * tridiag_max_eig(a, off);  // safety factor 1.1 on the estimate
-    }
     const double lmin = lmax / o.cheb_range;
     const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
     S.cheb_deg = o.cheb_degree;

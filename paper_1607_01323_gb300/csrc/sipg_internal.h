@@ -84,6 +84,8 @@ struct Mesh {
   // cached CG workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // cached multigrid hierarchy (mg.cu), dropped when degree or penalty change
+  void* mg = nullptr;
   ~Mesh();
 };
 
@@ -146,6 +148,22 @@ int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int nco
 int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s,
                      int* iters, double* relres);
 size_t noalloc_scratch_bytes();
+
+// Extreme Ritz values of D^-1 A (A as selected by o.op, D = diag(A)) from
+// `steps` Jacobi-PCG iterations on A y = b (Lanczos from the CG coefficients);
+// stops early when ||r|| <= rtol ||b||.  Uses the mesh's CG workspace.
+int lanczos_extremes(Mesh& m, const sipg_cg_opts& o, const double* b, int ncomp, int steps, double rtol,
+                     cudaStream_t s, double* ritz_min, double* ritz_max);
+
+// Geometric multigrid (mg.cu): set-up (cached on the mesh), one V-cycle
+// z = V(r) (skip / mean / ap / part as for the CG preconditioner, may be null),
+// hierarchy description and release.
+int mg_setup(Mesh& m, const sipg_cg_opts& o, cudaStream_t s);
+int mg_vcycle(Mesh& m, const double* r, double* z, const double* ap, const int* skip, const double* mean,
+              double* part, cudaStream_t s);
+int mg_info(const Mesh& m, int max_levels, int* nlevels, int* n_cells, double* lmax, double* coarse_lmin,
+            int* coarse_degree);
+void mg_release(Mesh& m);
 
 // profiling helpers (api.cpp)
 void prof_begin(Mesh& m, cudaStream_t s, cudaEvent_t* e0);

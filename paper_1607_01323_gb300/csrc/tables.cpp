@@ -141,6 +141,17 @@ double map_coord(const sipg_mesh_desc& d, int dir, double s) {
     double t = std::tanh(d.gamma * (2.0 * s - 1.0)) / std::tanh(d.gamma);
     return lo + (hi - lo) * 0.5 * (1.0 + t);
   }
+  if (d.map == SIPG_MAP_CHANNEL_LINEAR && dir == 1) {
+    // graded vertices eta_j = j / n, straight in between
+    const int n = d.n[1];
+    int j = (int)std::floor(s * n);
+    j = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+    const double e0 = (double)j / n, e1 = (double)(j + 1) / n;
+    const double y0 = std::tanh(d.gamma * (2.0 * e0 - 1.0)) / std::tanh(d.gamma);
+    const double y1 = std::tanh(d.gamma * (2.0 * e1 - 1.0)) / std::tanh(d.gamma);
+    const double t = y0 + (y1 - y0) * (s - e0) * n;
+    return lo + (hi - lo) * 0.5 * (1.0 + t);
+  }
   return lo + (hi - lo) * s;
 }
 

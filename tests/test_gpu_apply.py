@@ -33,6 +33,10 @@ CASES = [
     ("neumann_channel_k3", channel((3, 4, 3), wall="neumann"), 3, 1.0),
     ("single_periodic_cell_k3", case((1, 1, 1)), 3, 1.0),
     ("all_dirichlet_k3", case((2, 3, 2), bc_lo=("dirichlet",) * 3, bc_hi=("dirichlet",) * 3), 3, 1.0),
+    # straight cells on graded vertices (coarse multigrid levels), down to one cell
+    ("channel_linear_k3", dict(channel((2, 4, 2)), mapping="channel_linear"), 3, 1.0),
+    ("channel_linear_single_cell_k4", dict(channel((1, 1, 1)), mapping="channel_linear"), 4, 1.0),
+    ("channel_linear_pair_k2", dict(channel((2, 2, 2), wall="neumann"), mapping="channel_linear"), 2, 1.0),
 ]
 
 
@@ -176,7 +180,10 @@ def test_helmholtz_f64_parity(k):
 
 def test_mass_inverse_mass_diagonal():
     from paper_1607_01323_gb300 import apply_inverse_mass_f64, apply_mass_f64, diagonal_f64
-    for c, k in [(channel((3, 4, 2)), 3), (case((2, 3, 2), bc_lo=("dirichlet",) * 3, bc_hi=("neumann",) * 3), 5)]:
+    # the last three have one cell across periodic directions (self-coupled faces)
+    for c, k in [(channel((3, 4, 2)), 3), (case((2, 3, 2), bc_lo=("dirichlet",) * 3, bc_hi=("neumann",) * 3), 5),
+                 (case((1, 1, 1)), 3), (case((1, 2, 3), hi=(0.5, 1.0, 2.0)), 2),
+                 (dict(channel((1, 1, 1)), mapping="channel_linear"), 4)]:
         op = SIPG(oracle_spec(c), k)
         m = gpu_mesh(c, k)
         N = m.n_dofs
