@@ -315,6 +315,32 @@ def run_ours(args):
         e2e_iters += r2.iters + 1
     e2e_value = world * e2e_iters * N / (e2e_ms / 1e3)
 
+    # the same solve with the multigrid preconditioner of Sec. 5.1 (outside the
+    # timed steps; its set-up -- level tables, diagonals, Lanczos estimates, the
+    # dense coarse operator -- is built once and cached on the mesh)
+    from paper_1607_01323_gb300 import mg_setup
+    mg_opts = dict(precond="gmg_f32", rtol=RTOL, use_graph=1, check_every=CHECK_EVERY)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
+    mg_info = mg_setup(m, precond="gmg_f32")
+    mg_setup_ms = 1e3 * (time.perf_counter() - t_setup)
+    for _ in range(2):
+        x.zero_()
+        cg_solve(m, b, x, **mg_opts)
+    torch.cuda.synchronize()
+    mg_ms, mg_iters = [], 0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        x.zero_()
+        e0.record()
+        _, rm = cg_solve(m, b, x, **mg_opts)
+        e1.record()
+        torch.cuda.synchronize()
+        mg_ms.append(e0.elapsed_time(e1))
+        mg_iters = rm.iters
+        if not rm.converged:
+            raise SystemExit("multigrid solve did not converge: %r" % rm)
+
     # FP32 operator apply throughput on the same mesh (outside the timed step)
     x32 = b.float()
     y32 = torch.empty_like(x32)
@@ -386,6 +412,11 @@ def run_ours(args):
                      "hbm": {"achieved_gbs": bytes_apply / (avg_apply_ms / 1e3) / 1e9, "peak_gbs": hbm,
                              "frac": (bytes_apply / (avg_apply_ms / 1e3) / 1e9) / hbm if hbm else None,
                              "bytes_per_dof": 16}},
+        "gmg_solve": {"ms": sum(mg_ms) / len(mg_ms), "cg_iters": mg_iters, "setup_ms": mg_setup_ms,
+                      "levels": mg_info["n_cells"], "coarse_degree": mg_info["coarse_degree"],
+                      "speedup_vs_jacobi": (t_total * 1e3 / args.steps) / (sum(mg_ms) / len(mg_ms)),
+                      "note": "CG with one FP32 geometric-multigrid V-cycle per iteration (Chebyshev degree 5, "
+                              "range 20), same rhs and tolerance; set-up cached and not timed"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
         "gpu_launches": launches,
         "clocks": clk,
@@ -419,6 +450,30 @@ def run_apply_only(args):
         ev[1].record()
         torch.cuda.synchronize()
         print("apply %s n=%s k=%d dofs=%d: %.4f ms" % (args.precision, n, k, m.n_dofs, ev[0].elapsed_time(ev[1])))
+
+
+def run_vcycle_only(args):
+    """Multigrid set-up and a few V-cycles on the bench mesh (or --cells/--k),
+    timed with CUDA events; for ncu launch lists of the V-cycle."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1607_01323_gb300 import Mesh, mg_setup, mg_vcycle
+    w = dict(WORKLOAD)
+    n = (args.cells,) * 3 if args.cells else w["n"]
+    k = args.k if args.k else w["k"]
+    m = Mesh(n, w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"], k=k)
+    info = mg_setup(m, precond="gmg_f32")
+    r = torch.rand(m.n_dofs, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for i in range(args.reps):
+        ev[0].record()
+        mg_vcycle(m, r, z)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print("vcycle n=%s k=%d dofs=%d levels=%d coarse_degree=%d: %.4f ms" % (
+            n, k, m.n_dofs, info["nlevels"], info["coarse_degree"], ev[0].elapsed_time(ev[1])))
 
 
 def _timed(fn, reps=3):
@@ -544,7 +599,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply"], help="apply: only operator applies")
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "vcycle"],
+                    help="apply: only operator applies; vcycle: only multigrid V-cycles")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--cells", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
@@ -556,6 +612,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "apply":
         run_apply_only(args)
+    elif args.mode == "vcycle":
+        run_vcycle_only(args)
     elif args.workload != "c2":
         run_config(args)
     elif args.impl == "reference":

@@ -54,10 +54,10 @@ __device__ __forceinline__ double cvt_out<double, dfl>(dfl v) {
 
 template <int P>
 struct LayerOff {
-  static constexpr int M = 0, K = P * P, Mi = 2 * P * P, Kc = 3 * P * P, dL = 4 * P * P, dR = 4 * P * P + P,
-                       dLh = 4 * P * P + 2 * P, dRh = 4 * P * P + 3 * P, h = 4 * P * P + 4 * P,
-                       t = 4 * P * P + 4 * P + 1, ts = 4 * P * P + 4 * P + 2, dTL = 4 * P * P + 4 * P + 3,
-                       dTR = 4 * P * P + 4 * P + 4, stride = 4 * P * P + 4 * P + 8;
+  static constexpr int RM = (P * P + 3) / 4 * 4, RV = (P + 3) / 4 * 4;  // padded block sizes (lmat, lvec)
+  static constexpr int M = 0, K = RM, Mi = 2 * RM, Kc = 3 * RM, dL = 4 * RM, dR = 4 * RM + RV, dLh = 4 * RM + 2 * RV,
+                       dRh = 4 * RM + 3 * RV, h = 4 * RM + 4 * RV, t = 4 * RM + 4 * RV + 1, ts = 4 * RM + 4 * RV + 2,
+                       dTL = 4 * RM + 4 * RV + 3, dTR = 4 * RM + 4 * RV + 4, stride = 4 * RM + 4 * RV + 8;
 };
 
 // Neighbour across side (0 = low, 1 = high) of direction dir.  kind: 0 interior
@@ -193,6 +193,71 @@ template <int P>
 __device__ __forceinline__ void matvec(dfl (&out)[P], const dfl* __restrict__ A, const dfl (&v)[P]) {
 #pragma unroll
   for (int a = 0; a < P; ++a) out[a] = df_dot<P>(A + a * P, v);
+}
+
+// FP32 versions reading the 16-byte aligned table blocks with 128-bit loads
+// (four entries per load instruction); the FMAs run in the same order as the
+// generic versions, so the results are identical.
+template <int P>
+__device__ __forceinline__ void matvec(float (&out)[P], const float* __restrict__ A, const float (&v)[P]) {
+  constexpr int N4 = (P * P + 3) / 4;
+  const float4* __restrict__ A4 = reinterpret_cast<const float4*>(A);
+#pragma unroll
+  for (int a = 0; a < P; ++a) out[a] = 0.f;
+#pragma unroll
+  for (int q = 0; q < N4; ++q) {
+    const float4 f = A4[q];
+    const float e[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * q + j;
+      if (k < P * P) out[k / P] = fmaf(e[j], v[k % P], out[k / P]);
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ float dotp(const float* __restrict__ a, const float (&v)[P]) {
+  constexpr int N4 = (P + 3) / 4;
+  const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a);
+  float s = 0.f;
+#pragma unroll
+  for (int q = 0; q < N4; ++q) {
+    const float4 f = a4[q];
+    const float e[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (4 * q + j < P) s = fmaf(e[j], v[4 * q + j], s);
+  }
+  return s;
+}
+
+// w += c * (table vector block d): FP32 reads the block with 128-bit loads,
+// the other types stream it entry by entry (fewer live registers)
+template <typename T, int P>
+__device__ __forceinline__ void axpy_vec(T (&w)[P], const T* __restrict__ d, T c) {
+#pragma unroll
+  for (int a = 0; a < P; ++a) w[a] = fma(d[a], c, w[a]);
+}
+template <int P>
+__device__ __forceinline__ void load_vec(float (&out)[P], const float* __restrict__ src) {
+  constexpr int N4 = (P + 3) / 4;
+  const float4* __restrict__ s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int q = 0; q < N4; ++q) {
+    const float4 f = s4[q];
+    const float e[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (4 * q + j < P) out[4 * q + j] = e[j];
+  }
+}
+template <int P>
+__device__ __forceinline__ void axpy_vec(float (&w)[P], const float* __restrict__ d, float c) {
+  float dv[P];
+  load_vec(dv, d);
+#pragma unroll
+  for (int a = 0; a < P; ++a) w[a] = fmaf(dv[a], c, w[a]);
 }
 
 // Index of element (a, b, c) inside one cell.
@@ -505,9 +570,7 @@ __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* _
     const T gn = dotp(LR + O::dLh, uR);
     const T J = u[P - 1] - uR[0];
     w[P - 1] += fma(tauFR, J, -gn);
-    const T ur = uR[0];
-#pragma unroll
-    for (int a = 0; a < P; ++a) w[a] = fma(L[O::dRh + a], ur, w[a]);
+    axpy_vec(w, L + O::dRh, uR[0]);
   } else if (kindR == SIPG_BC_DIRICHLET) {
     w[P - 1] = fma(tau2e, u[P - 1], w[P - 1]);
   }
@@ -515,9 +578,7 @@ __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* _
     const T gn = dotp(LL + O::dRh, uL);
     const T J = uL[P - 1] - u[0];
     w[0] += fma(-tauFL, J, gn);
-    const T ul = -uL[P - 1];
-#pragma unroll
-    for (int a = 0; a < P; ++a) w[a] = fma(L[O::dLh + a], ul, w[a]);
+    axpy_vec(w, L + O::dLh, -uL[P - 1]);
   } else if (kindL == SIPG_BC_DIRICHLET) {
     w[0] = fma(tau2e, u[0], w[0]);
   }
@@ -538,11 +599,19 @@ struct UniformMinBlocks {
                                : (std::is_same<T, float>::value ? (P <= 6 ? 4 : (P == 7 ? 3 : 2)) : (P <= 6 ? 2 : 1));
 };
 
-template <typename T, typename S, int P>
+// Shared memory of apply_uniform_kernel: own cells and two line-result buffers.
+template <typename T, int P>
+__host__ __device__ constexpr size_t uniform_smem_bytes(int cpb) {
+  return (size_t)3 * cpb * P * P * P * sizeof(T);
+}
+
+// CHEB (FP32 only): instead of storing y = A x, apply one Chebyshev step of the
+// multigrid smoother to the block's own unknowns with x = d (see ChebEpi).
+template <typename T, typename S, int P, bool CHEB = false>
 __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value) apply_uniform_kernel(Geo<T> g, const S* __restrict__ x,
                                                                         S* __restrict__ y, int cpb, T mass_rel,
                                                                         T scale, int do_scale, int do_mass,
-                                                                        DotSink sink) {
+                                                                        DotSink sink, ChebEpi epi) {
   if (sink.skip && *sink.skip) return;
   double* dots = sink.partials;
   using O = LayerOff<P>;
@@ -669,14 +738,32 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     load_line<T, P>(v, w2, start, step);
     matvec(out, Mx, v);
     load_line<T, P>(r1, w1, start, step);
-    S* yo = y + cbase + (long long)e * P3 + start;
+    if constexpr (CHEB) {
+      static_assert(std::is_same<T, float>::value && std::is_same<S, float>::value, "FP32 only");
+      // t = A d for this x-line; d (the input) is read again (cached)
+      T dold[P];
+      load_line_global_cvt<T, S, P>(dold, xc + (long long)e * P3, start, step);
+      const long long o = cbase + (long long)e * P3 + start;
 #pragma unroll
-    for (int a = 0; a < P; ++a) {
-      out[a] += r1[a];
-      if (do_scale) out[a] *= scale;
-      yo[a] = cvt_out<S, T>(out[a]);
+      for (int a = 0; a < P; ++a) {
+        T tt = out[a] + r1[a];
+        if (do_scale) tt *= scale;
+        const float ri = epi.r[o + a] - tt;
+        const float di = epi.c1 * dold[a] + epi.c2 * ri * epi.dinv[o + a];
+        epi.r[o + a] = ri;
+        epi.dnew[o + a] = di;
+        epi.x[o + a] += di;
+      }
+    } else {
+      S* yo = y + cbase + (long long)e * P3 + start;
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        out[a] += r1[a];
+        if (do_scale) out[a] *= scale;
+        yo[a] = cvt_out<S, T>(out[a]);
+      }
     }
-    if (dots) {
+    if (!CHEB && dots) {
       // line sums in the compute type, one conversion per line; the x-line of
       // the input is read again (cached) instead of being held in registers
       T ux[P];

@@ -38,9 +38,9 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
   const Geo<T> g = make_geo<T>(m);
   const dim3 grid((unsigned)((m.ncell + cpb - 1) / cpb), (unsigned)ncomp);
   const int threads = (cpb * P * P + 31) / 32 * 32;  // whole warps (the block reduction shuffles full warps)
-  const size_t smem = (size_t)3 * cpb * P * P * P * sizeof(T);
-  if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
   const bool uniform = stiff && nu_cell == nullptr;
+  const size_t smem = uniform ? uniform_smem_bytes<T, P>(cpb) : (size_t)3 * cpb * P * P * P * sizeof(T);
+  if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
   const DotSink ds = sink ? *sink : DotSink();
   if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
     cudaError_t e = uniform ? cudaFuncSetAttribute(apply_uniform_kernel<T, T, P>,
@@ -61,14 +61,15 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
           if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
         }
         apply_uniform_kernel<dfl, double, P><<<grid, threads, smem, s>>>(gd, x, y, cpb, dfl(cm / nu), dfl(nu),
-                                                                         do_scale, do_mass, ds);
+                                                                         do_scale, do_mass, ds, ChebEpi());
         if (nblocks) *nblocks = (int)(grid.x * grid.y);
         const_cast<Mesh&>(m).launches++;
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch");
       }
     }
-    apply_uniform_kernel<T, T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm / nu, nu, do_scale, do_mass, ds);
+    apply_uniform_kernel<T, T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm / nu, nu, do_scale, do_mass, ds,
+                                                              ChebEpi());
   } else {
     if constexpr (std::is_same<T, double>::value) {
       if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {

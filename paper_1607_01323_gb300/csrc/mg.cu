@@ -47,6 +47,13 @@ namespace {
 constexpr int kVB = 152 * 8;  // vector-kernel grid (the CG reads kVB partial sums)
 constexpr int kVT = 256;
 constexpr int kMaxLevels = 32;
+constexpr long long kDenseCoarseMax = 6144;  // coarsest unknowns for the precomputed coarse operator (151 MB)
+
+// grid of a non-reducing vector kernel: no more blocks than the vector needs
+inline unsigned vec_grid(long long n) {
+  const long long b = (n + kVT - 1) / kVT;
+  return (unsigned)(b < 1 ? 1 : (b > kVB ? kVB : b));
+}
 
 struct MgKey {
   int k = -1;
@@ -65,8 +72,11 @@ struct MgLevel {
   long long n = 0;       // unknowns
   int fac[3] = {1, 1, 1};  // halving factor towards the next coarser level
   float *dinv = nullptr, *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
+  float* d2 = nullptr;      // second direction buffer (the fused steps ping-pong d)
+  float* dlast = nullptr;   // buffer holding the latest direction of the pre-smoother
   double lmin = 0.0, lmax = 0.0;  // Chebyshev interval of this level
   int degree = 0;                 // Chebyshev steps (smoother or coarse solve)
+  float* Q = nullptr;             // coarsest level: the coarse Chebyshev operator as a dense matrix
   float inv_theta = 0.f;
   std::vector<float> c1, c2;      // recurrence coefficients per step
 };
@@ -78,9 +88,11 @@ struct Hierarchy {
   float* emb = nullptr;  // [3][P][P]: child 0, child 1, identity
   void* mem = nullptr;   // FP32 level vectors and two FP64 scratch vectors
   double *tmp_a = nullptr, *tmp_b = nullptr;
+  float* Qmem = nullptr;
   ~Hierarchy() {
     if (mem) cudaFree(mem);
     if (emb) cudaFree(emb);
+    if (Qmem) cudaFree(Qmem);
   }
 };
 
@@ -198,10 +210,77 @@ __global__ void k_mg_random(long long n, unsigned long long seed, double* __rest
   }
 }
 
+// ------------------------------------------------------------ dense coarse solve
+// The coarse Chebyshev iteration from zero is a fixed polynomial in D^-1 A:
+// x = Q b with Q = q(D^-1 A) D^-1.  For a small coarsest level Q is formed
+// once, column by column, by running the same iteration in FP64 on the
+// columns of the identity (one operator product on all columns at a time),
+// and the cycle applies it as one dense product.
+__global__ void k_q_start(long long n, const double* __restrict__ dinv, double* __restrict__ r,
+                          double* __restrict__ d, double* __restrict__ x, double inv_theta) {
+  const long long nn = n * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
+    const long long col = i / n, j = i - col * n;  // vector `col`, entry j
+    const double bi = j == col ? 1.0 : 0.0;
+    const double di = bi * dinv[j] * inv_theta;
+    r[i] = bi;
+    d[i] = di;
+    x[i] = di;
+  }
+}
+
+__global__ void k_q_step(long long n, const double* __restrict__ t, const double* __restrict__ dinv,
+                         double* __restrict__ r, double* __restrict__ d, double* __restrict__ x, double c1,
+                         double c2) {
+  const long long nn = n * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i % n;
+    const double ri = r[i] - t[i];
+    const double di = c1 * d[i] + c2 * ri * dinv[j];
+    r[i] = ri;
+    d[i] = di;
+    x[i] += di;
+  }
+}
+
+// Q[i][j] = (result for b = e_j)[i]: row-major FP32 copy of the transpose
+__global__ void k_q_store(long long n, const double* __restrict__ x, float* __restrict__ Q) {
+  const long long nn = n * n;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += (long long)gridDim.x * blockDim.x) {
+    const long long i = k / n, j = k - i * n;
+    Q[k] = (float)x[j * n + i];
+  }
+}
+
+__global__ void k_inv64(long long n, const double* __restrict__ diag, double* __restrict__ dinv) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dinv[i] = 1.0 / diag[i];
+}
+
+// x = Q b, one warp per row (coalesced along the row), b staged in shared memory
+__global__ void k_mg_dense(const int* __restrict__ skip, int n, const float* __restrict__ Q,
+                           const float* __restrict__ b, float* __restrict__ x) {
+  if (skip && *skip) return;
+  extern __shared__ float sb[];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) sb[j] = b[j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  const float* q = Q + (long long)row * n;
+  float acc = 0.f;
+  for (int j = lane; j < n; j += 32) acc = fmaf(q[j], sb[j], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[row] = acc;
+}
+
 // ------------------------------------------------------------ transfer kernels
+constexpr int kTransferThreads = 512;
+
 struct MgDims {
   int nf[3], nc[3], fac[3];
   long long ncc;  // coarse cells
+  int nch;        // children per parent: fac[0] * fac[1] * fac[2]
   int cpb;        // coarse cells per block
 };
 
@@ -210,202 +289,207 @@ __device__ __forceinline__ long long fine_cell(const MgDims& g, int cx, int cy, 
   return ((long long)fz * g.nf[1] + fy) * g.nf[0] + fx;
 }
 
+// Thread layout of both transfer kernels: per coarse cell nch * P^2 threads,
+// one 1D line of one child each, so that the children are processed at once.
+struct TransferThread {
+  int lc, h, l, rem;  // cell slot in the block, child, line, rank within the cell
+  bool active;
+  long long cell;
+  int c[3], hh[3];    // coarse cell and child offsets
+};
+
+template <int P>
+__device__ __forceinline__ TransferThread transfer_thread(const MgDims& g) {
+  constexpr int P2 = P * P;
+  TransferThread t;
+  const int per = g.nch * P2;
+  t.lc = threadIdx.x / per;
+  t.rem = threadIdx.x - t.lc * per;
+  t.h = t.rem / P2;
+  t.l = t.rem - t.h * P2;
+  t.cell = (long long)blockIdx.x * g.cpb + t.lc;
+  t.active = t.lc < g.cpb && t.cell < g.ncc;
+  t.c[0] = t.c[1] = t.c[2] = 0;
+  if (t.active) {
+    t.c[0] = (int)(t.cell % g.nc[0]);
+    t.c[1] = (int)((t.cell / g.nc[0]) % g.nc[1]);
+    t.c[2] = (int)(t.cell / ((long long)g.nc[0] * g.nc[1]));
+  }
+  t.hh[0] = t.h % g.fac[0];
+  t.hh[1] = (t.h / g.fac[0]) % g.fac[1];
+  t.hh[2] = t.h / (g.fac[0] * g.fac[1]);
+  return t;
+}
+
 // Restriction of the residual r_f - t_f (t_f = A d, the last smoothing product)
 // to the parent cells: b_c = sum over children of (E_z^T (x) E_y^T (x) E_x^T)
-// (r_f - t_f)_child, written together with the coarse smoother's start
-// r = b, d = x = D^-1 b / theta.
+// (r_f - t_f)_child (children summed in a fixed order), written together with
+// the coarse smoother's start r = b, d = x = D^-1 b / theta.
 template <int P>
-__global__ void __launch_bounds__(kMaxCellThreads) k_mg_restrict(const int* __restrict__ skip, MgDims g,
-                                                                 const float* __restrict__ rf,
-                                                                 const float* __restrict__ tf,
-                                                                 const float* __restrict__ emb,
-                                                                 float* __restrict__ b, float* __restrict__ r,
-                                                                 float* __restrict__ d, float* __restrict__ x,
-                                                                 const float* __restrict__ dinv, float inv_theta) {
+__global__ void __launch_bounds__(kTransferThreads) k_mg_restrict(const int* __restrict__ skip, MgDims g,
+                                                                  const float* __restrict__ rf,
+                                                                  const float* __restrict__ tf,
+                                                                  const float* __restrict__ emb,
+                                                                  float* __restrict__ b, float* __restrict__ r,
+                                                                  float* __restrict__ d, float* __restrict__ x,
+                                                                  const float* __restrict__ dinv, float inv_theta) {
   if (skip && *skip) return;
   constexpr int P2 = P * P, P3 = P * P * P;
   extern __shared__ float sm[];
-  float* E = sm;                      // [3][P][P]
-  float* A = sm + 3 * P2;             // [cpb][P3]
-  float* B = A + (size_t)g.cpb * P3;  // [cpb][P3]
+  float* E = sm;                                      // [3][P][P]
+  float* A = sm + 3 * P2;                             // [cpb][nch][P3]
+  float* B = A + (size_t)g.cpb * g.nch * P3;          // [cpb][nch][P3]
   for (int i = threadIdx.x; i < 3 * P2; i += blockDim.x) E[i] = emb[i];
-  const int lc = threadIdx.x / P2, l = threadIdx.x % P2;
-  const long long cell = (long long)blockIdx.x * g.cpb + lc;
-  const bool active = lc < g.cpb && cell < g.ncc;
-  int cx = 0, cy = 0, cz = 0;
-  if (active) {
-    cx = (int)(cell % g.nc[0]);
-    cy = (int)((cell / g.nc[0]) % g.nc[1]);
-    cz = (int)(cell / ((long long)g.nc[0] * g.nc[1]));
+  const TransferThread t = transfer_thread<P>(g);
+  const size_t slot = (size_t)(t.lc < g.cpb ? t.lc : 0) * g.nch;
+  float* Ac = A + (slot + t.h) * P3;
+  float* Bc = B + (slot + t.h) * P3;
+  if (t.active) {
+    const long long f = fine_cell(g, t.c[0], t.c[1], t.c[2], t.hh[0], t.hh[1], t.hh[2]) * P3;
+    for (int i = t.l; i < P3; i += P2) Ac[i] = rf[f + i] - tf[f + i];
   }
-  float* Ac = A + (size_t)(lc < g.cpb ? lc : 0) * P3;
-  float* Bc = B + (size_t)(lc < g.cpb ? lc : 0) * P3;
-  float acc[P];
+  __syncthreads();
+  const float* Ex = E + (g.fac[0] == 2 ? t.hh[0] : 2) * P2;
+  const float* Ey = E + (g.fac[1] == 2 ? t.hh[1] : 2) * P2;
+  const float* Ez = E + (g.fac[2] == 2 ? t.hh[2] : 2) * P2;
+  if (t.active) {  // x lines (b, c): B[c][b][a'] = sum_a Ex[a][a'] A[c][b][a]
+    const int bb = t.l % P, cc = t.l / P;
+    float u[P];
 #pragma unroll
-  for (int c = 0; c < P; ++c) acc[c] = 0.f;
-  for (int hz = 0; hz < g.fac[2]; ++hz)
-    for (int hy = 0; hy < g.fac[1]; ++hy)
-      for (int hx = 0; hx < g.fac[0]; ++hx) {
-        __syncthreads();  // E loaded / previous child's z phase done with A
-        if (active) {
-          const long long f = fine_cell(g, cx, cy, cz, hx, hy, hz) * P3;
-          for (int i = l; i < P3; i += P2) Ac[i] = rf[f + i] - tf[f + i];
-        }
-        __syncthreads();
-        const float* Ex = E + (g.fac[0] == 2 ? hx : 2) * P2;
-        const float* Ey = E + (g.fac[1] == 2 ? hy : 2) * P2;
-        const float* Ez = E + (g.fac[2] == 2 ? hz : 2) * P2;
-        if (active) {  // x lines (b, c): B[c][b][a'] = sum_a Ex[a][a'] A[c][b][a]
-          const int bb = l % P, cc = l / P;
-          float u[P];
+    for (int a = 0; a < P; ++a) u[a] = Ac[(cc * P + bb) * P + a];
 #pragma unroll
-          for (int a = 0; a < P; ++a) u[a] = Ac[(cc * P + bb) * P + a];
+    for (int a2 = 0; a2 < P; ++a2) {
+      float sacc = 0.f;
 #pragma unroll
-          for (int a2 = 0; a2 < P; ++a2) {
-            float s = 0.f;
+      for (int a = 0; a < P; ++a) sacc = fmaf(Ex[a * P + a2], u[a], sacc);
+      Bc[(cc * P + bb) * P + a2] = sacc;
+    }
+  }
+  __syncthreads();
+  if (t.active) {  // y lines (a', c): A[c][b'][a'] = sum_b Ey[b][b'] B[c][b][a']
+    const int aa = t.l % P, cc = t.l / P;
+    float u[P];
 #pragma unroll
-            for (int a = 0; a < P; ++a) s = fmaf(Ex[a * P + a2], u[a], s);
-            Bc[(cc * P + bb) * P + a2] = s;
-          }
-        }
-        __syncthreads();
-        if (active) {  // y lines (a', c): A[c][b'][a'] = sum_b Ey[b][b'] B[c][b][a']
-          const int aa = l % P, cc = l / P;
-          float u[P];
+    for (int bq = 0; bq < P; ++bq) u[bq] = Bc[(cc * P + bq) * P + aa];
 #pragma unroll
-          for (int bq = 0; bq < P; ++bq) u[bq] = Bc[(cc * P + bq) * P + aa];
+    for (int b2 = 0; b2 < P; ++b2) {
+      float sacc = 0.f;
 #pragma unroll
-          for (int b2 = 0; b2 < P; ++b2) {
-            float s = 0.f;
+      for (int bq = 0; bq < P; ++bq) sacc = fmaf(Ey[bq * P + b2], u[bq], sacc);
+      Ac[(cc * P + b2) * P + aa] = sacc;
+    }
+  }
+  __syncthreads();
+  if (t.active) {  // z lines (a', b'): B[c'][b'][a'] = sum_c Ez[c][c'] A[c][b'][a']
+    const int aa = t.l % P, bb = t.l / P;
+    float u[P];
 #pragma unroll
-            for (int bq = 0; bq < P; ++bq) s = fmaf(Ey[bq * P + b2], u[bq], s);
-            Ac[(cc * P + b2) * P + aa] = s;
-          }
-        }
-        __syncthreads();
-        if (active) {  // z lines (a', b'): acc[c'] += sum_c Ez[c][c'] A[c][b'][a']
-          const int aa = l % P, bb = l / P;
-          float u[P];
+    for (int cq = 0; cq < P; ++cq) u[cq] = Ac[(cq * P + bb) * P + aa];
 #pragma unroll
-          for (int cq = 0; cq < P; ++cq) u[cq] = Ac[(cq * P + bb) * P + aa];
+    for (int c2 = 0; c2 < P; ++c2) {
+      float sacc = 0.f;
 #pragma unroll
-          for (int c2 = 0; c2 < P; ++c2) {
-            float s = acc[c2];
-#pragma unroll
-            for (int cq = 0; cq < P; ++cq) s = fmaf(Ez[cq * P + c2], u[cq], s);
-            acc[c2] = s;
-          }
-        }
-      }
-  if (active) {
-    const int aa = l % P, bb = l / P;
-    const long long o = cell * P3 + bb * P + aa;
-#pragma unroll
-    for (int c = 0; c < P; ++c) {
-      const long long i = o + (long long)c * P2;
-      const float bi = acc[c];
-      const float di = bi * dinv[i] * inv_theta;
-      b[i] = bi;
-      r[i] = bi;
-      d[i] = di;
-      x[i] = di;
+      for (int cq = 0; cq < P; ++cq) sacc = fmaf(Ez[cq * P + c2], u[cq], sacc);
+      Bc[(c2 * P + bb) * P + aa] = sacc;
+    }
+  }
+  __syncthreads();
+  if (t.active) {  // sum over the children (fixed order), coalesced writes
+    const float* Bs = B + slot * P3;
+    const int per = g.nch * P2;
+    for (int i = t.rem; i < P3; i += per) {
+      float bi = 0.f;
+      for (int hq = 0; hq < g.nch; ++hq) bi += Bs[(size_t)hq * P3 + i];
+      const long long o = t.cell * P3 + i;
+      const float di = bi * dinv[o] * inv_theta;
+      b[o] = bi;
+      r[o] = bi;
+      d[o] = di;
+      x[o] = di;
     }
   }
 }
 
 // Prolongation and correction: x_f(child) += (E_z (x) E_y (x) E_x) x_c(parent).
 template <int P>
-__global__ void __launch_bounds__(kMaxCellThreads) k_mg_prolong(const int* __restrict__ skip, MgDims g,
-                                                                const float* __restrict__ xc,
-                                                                const float* __restrict__ emb,
-                                                                float* __restrict__ xf) {
+__global__ void __launch_bounds__(kTransferThreads) k_mg_prolong(const int* __restrict__ skip, MgDims g,
+                                                                 const float* __restrict__ xc,
+                                                                 const float* __restrict__ emb,
+                                                                 float* __restrict__ xf) {
   if (skip && *skip) return;
   constexpr int P2 = P * P, P3 = P * P * P;
   extern __shared__ float sm[];
   float* E = sm;
-  float* C = sm + 3 * P2;             // parent values [cpb][P3]
-  float* A = C + (size_t)g.cpb * P3;  // [cpb][P3]
-  float* B = A + (size_t)g.cpb * P3;  // [cpb][P3]
+  float* C = sm + 3 * P2;                           // parent values [cpb][P3]
+  float* A = C + (size_t)g.cpb * P3;                // [cpb][nch][P3]
+  float* B = A + (size_t)g.cpb * g.nch * P3;        // [cpb][nch][P3]
   for (int i = threadIdx.x; i < 3 * P2; i += blockDim.x) E[i] = emb[i];
-  const int lc = threadIdx.x / P2, l = threadIdx.x % P2;
-  const long long cell = (long long)blockIdx.x * g.cpb + lc;
-  const bool active = lc < g.cpb && cell < g.ncc;
-  int cx = 0, cy = 0, cz = 0;
-  float* Cc = C + (size_t)(lc < g.cpb ? lc : 0) * P3;
-  float* Ac = A + (size_t)(lc < g.cpb ? lc : 0) * P3;
-  float* Bc = B + (size_t)(lc < g.cpb ? lc : 0) * P3;
-  if (active) {
-    cx = (int)(cell % g.nc[0]);
-    cy = (int)((cell / g.nc[0]) % g.nc[1]);
-    cz = (int)(cell / ((long long)g.nc[0] * g.nc[1]));
-    for (int i = l; i < P3; i += P2) Cc[i] = xc[cell * P3 + i];
+  const TransferThread t = transfer_thread<P>(g);
+  const int lcs = t.lc < g.cpb ? t.lc : 0;
+  float* Cc = C + (size_t)lcs * P3;
+  float* Ac = A + ((size_t)lcs * g.nch + t.h) * P3;
+  float* Bc = B + ((size_t)lcs * g.nch + t.h) * P3;
+  if (t.active) {
+    const int per = g.nch * P2;
+    for (int i = t.rem; i < P3; i += per) Cc[i] = xc[t.cell * P3 + i];
   }
-  for (int hz = 0; hz < g.fac[2]; ++hz)
-    for (int hy = 0; hy < g.fac[1]; ++hy)
-      for (int hx = 0; hx < g.fac[0]; ++hx) {
-        __syncthreads();  // C and E loaded / previous child's store done with A
-        const float* Ex = E + (g.fac[0] == 2 ? hx : 2) * P2;
-        const float* Ey = E + (g.fac[1] == 2 ? hy : 2) * P2;
-        const float* Ez = E + (g.fac[2] == 2 ? hz : 2) * P2;
-        if (active) {  // z lines (a, b): A[c][b][a] = sum_c' Ez[c][c'] C[c'][b][a]
-          const int aa = l % P, bb = l / P;
-          float u[P];
+  __syncthreads();
+  const float* Ex = E + (g.fac[0] == 2 ? t.hh[0] : 2) * P2;
+  const float* Ey = E + (g.fac[1] == 2 ? t.hh[1] : 2) * P2;
+  const float* Ez = E + (g.fac[2] == 2 ? t.hh[2] : 2) * P2;
+  if (t.active) {  // z lines (a, b): A[c][b][a] = sum_c' Ez[c][c'] C[c'][b][a]
+    const int aa = t.l % P, bb = t.l / P;
+    float u[P];
 #pragma unroll
-          for (int cq = 0; cq < P; ++cq) u[cq] = Cc[(cq * P + bb) * P + aa];
+    for (int cq = 0; cq < P; ++cq) u[cq] = Cc[(cq * P + bb) * P + aa];
 #pragma unroll
-          for (int c = 0; c < P; ++c) {
-            float s = 0.f;
+    for (int c = 0; c < P; ++c) {
+      float sacc = 0.f;
 #pragma unroll
-            for (int cq = 0; cq < P; ++cq) s = fmaf(Ez[c * P + cq], u[cq], s);
-            Ac[(c * P + bb) * P + aa] = s;
-          }
-        }
-        __syncthreads();
-        if (active) {  // y lines (a, c): B[c][b][a] = sum_b' Ey[b][b'] A[c][b'][a]
-          const int aa = l % P, cc = l / P;
-          float u[P];
+      for (int cq = 0; cq < P; ++cq) sacc = fmaf(Ez[c * P + cq], u[cq], sacc);
+      Ac[(c * P + bb) * P + aa] = sacc;
+    }
+  }
+  __syncthreads();
+  if (t.active) {  // y lines (a, c): B[c][b][a] = sum_b' Ey[b][b'] A[c][b'][a]
+    const int aa = t.l % P, cc = t.l / P;
+    float u[P];
 #pragma unroll
-          for (int bq = 0; bq < P; ++bq) u[bq] = Ac[(cc * P + bq) * P + aa];
+    for (int bq = 0; bq < P; ++bq) u[bq] = Ac[(cc * P + bq) * P + aa];
 #pragma unroll
-          for (int b2 = 0; b2 < P; ++b2) {
-            float s = 0.f;
+    for (int b2 = 0; b2 < P; ++b2) {
+      float sacc = 0.f;
 #pragma unroll
-            for (int bq = 0; bq < P; ++bq) s = fmaf(Ey[b2 * P + bq], u[bq], s);
-            Bc[(cc * P + b2) * P + aa] = s;
-          }
-        }
-        __syncthreads();
-        if (active) {  // x lines (b, c): A[c][b][a] = sum_a' Ex[a][a'] B[c][b][a']
-          const int bb = l % P, cc = l / P;
-          float u[P];
+      for (int bq = 0; bq < P; ++bq) sacc = fmaf(Ey[b2 * P + bq], u[bq], sacc);
+      Bc[(cc * P + b2) * P + aa] = sacc;
+    }
+  }
+  __syncthreads();
+  if (t.active) {  // x lines (b, c): A[c][b][a] = sum_a' Ex[a][a'] B[c][b][a']
+    const int bb = t.l % P, cc = t.l / P;
+    float u[P];
 #pragma unroll
-          for (int a = 0; a < P; ++a) u[a] = Bc[(cc * P + bb) * P + a];
+    for (int a = 0; a < P; ++a) u[a] = Bc[(cc * P + bb) * P + a];
 #pragma unroll
-          for (int a2 = 0; a2 < P; ++a2) {
-            float s = 0.f;
+    for (int a2 = 0; a2 < P; ++a2) {
+      float sacc = 0.f;
 #pragma unroll
-            for (int a = 0; a < P; ++a) s = fmaf(Ex[a2 * P + a], u[a], s);
-            Ac[(cc * P + bb) * P + a2] = s;
-          }
-        }
-        __syncthreads();
-        if (active) {  // coalesced read-modify-write of the child
-          const long long f = fine_cell(g, cx, cy, cz, hx, hy, hz) * P3;
-          for (int i = l; i < P3; i += P2) xf[f + i] += Ac[i];
-        }
-      }
-}
-
-int transfer_cpb(int p) {
-  int c = kMaxCellThreads / (p * p);
-  return c < 1 ? 1 : c;
+      for (int a = 0; a < P; ++a) sacc = fmaf(Ex[a2 * P + a], u[a], sacc);
+      Ac[(cc * P + bb) * P + a2] = sacc;
+    }
+  }
+  __syncthreads();
+  if (t.active) {  // coalesced read-modify-write of the child
+    const long long f = fine_cell(g, t.c[0], t.c[1], t.c[2], t.hh[0], t.hh[1], t.hh[2]) * P3;
+    for (int i = t.l; i < P3; i += P2) xf[f + i] += Ac[i];
+  }
 }
 
 template <int P>
 int launch_restrict_p(const MgDims& g, const int* skip, const float* rf, const float* tf, const float* emb, float* b,
                       float* r, float* d, float* x, const float* dinv, float inv_theta, cudaStream_t s) {
-  const int threads = (g.cpb * P * P + 31) / 32 * 32;
-  const size_t smem = (size_t)(3 * P * P + 2 * g.cpb * P * P * P) * sizeof(float);
+  const int threads = (g.cpb * g.nch * P * P + 31) / 32 * 32;
+  const size_t smem = (size_t)(3 * P * P + 2 * g.cpb * g.nch * P * P * P) * sizeof(float);
   const unsigned blocks = (unsigned)((g.ncc + g.cpb - 1) / g.cpb);
   k_mg_restrict<P><<<blocks, threads, smem, s>>>(skip, g, rf, tf, emb, b, r, d, x, dinv, inv_theta);
   cudaError_t e = cudaGetLastError();
@@ -414,8 +498,8 @@ int launch_restrict_p(const MgDims& g, const int* skip, const float* rf, const f
 
 template <int P>
 int launch_prolong_p(const MgDims& g, const int* skip, const float* xc, const float* emb, float* xf, cudaStream_t s) {
-  const int threads = (g.cpb * P * P + 31) / 32 * 32;
-  const size_t smem = (size_t)(3 * P * P + 3 * g.cpb * P * P * P) * sizeof(float);
+  const int threads = (g.cpb * g.nch * P * P + 31) / 32 * 32;
+  const size_t smem = (size_t)(3 * P * P + g.cpb * P * P * P + 2 * g.cpb * g.nch * P * P * P) * sizeof(float);
   const unsigned blocks = (unsigned)((g.ncc + g.cpb - 1) / g.cpb);
   k_mg_prolong<P><<<blocks, threads, smem, s>>>(skip, g, xc, emb, xf);
   cudaError_t e = cudaGetLastError();
@@ -462,7 +546,9 @@ MgDims dims_of(const MgLevel& fine, const MgLevel& coarse, int p) {
     g.fac[d] = fine.fac[d];
   }
   g.ncc = coarse.mesh->ncell;
-  g.cpb = transfer_cpb(p);
+  g.nch = g.fac[0] * g.fac[1] * g.fac[2];
+  const int per = g.nch * p * p;  // <= 8 * 64 = kTransferThreads
+  g.cpb = kTransferThreads / per;
   return g;
 }
 
@@ -514,6 +600,72 @@ int level_apply(Mesh& m, const MgLevel& L, const float* v, float* t, const int* 
   ds.sums = 0;
   const long long before = L.mesh->launches;
   int st = launch_apply<float>(*L.mesh, v, t, 1, 0.f, 1.f, nullptr, true, &ds, nullptr, s);
+  if (L.mesh != &m) m.launches += L.mesh->launches - before;
+  return st;
+}
+
+// Q = q(D^-1 A) D^-1 of the coarse Chebyshev iteration (see k_q_start); the
+// level's diagonal is in h.tmp_b.
+int build_dense_coarse(Mesh& m, Hierarchy& h, MgLevel& L, cudaStream_t s) {
+  const long long nc = L.n, nn = nc * nc;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMalloc(&tmp, (size_t)(4 * nn + nc) * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SIPG_ENOMEM, "cudaMalloc for the dense coarse operator failed");
+  }
+  double *R = tmp, *D = tmp + nn, *X = tmp + 2 * nn, *T = tmp + 3 * nn, *dinv = tmp + 4 * nn;
+  int st = SIPG_OK;
+  k_inv64<<<vec_grid(nc), kVT, 0, s>>>(nc, h.tmp_b, dinv);
+  st = vec_launched(m);
+  const double theta = 0.5 * (L.lmax + L.lmin), delta = 0.5 * (L.lmax - L.lmin), sigma = theta / delta;
+  if (!st) {
+    k_q_start<<<kVB, kVT, 0, s>>>(nc, dinv, R, D, X, 1.0 / theta);
+    st = vec_launched(m);
+  }
+  double rho = 1.0 / sigma;
+  for (int step = 1; step < L.degree && !st; ++step) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    const double c1 = rn * rho, c2 = 2.0 * rn / delta;
+    rho = rn;
+    st = launch_apply<double>(*L.mesh, D, T, (int)nc, 0.0, 1.0, nullptr, true, nullptr, nullptr, s);
+    if (!st) {
+      k_q_step<<<kVB, kVT, 0, s>>>(nc, T, dinv, R, D, X, c1, c2);
+      st = vec_launched(m);
+    }
+  }
+  if (!st) {
+    e = cudaMalloc(&h.Qmem, (size_t)nn * sizeof(float));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h.Qmem = nullptr;
+      st = fail(SIPG_ENOMEM, "cudaMalloc for the dense coarse operator failed");
+    }
+  }
+  if (!st) {
+    k_q_store<<<kVB, kVT, 0, s>>>(nc, X, h.Qmem);
+    st = vec_launched(m);
+  }
+  e = cudaStreamSynchronize(s);
+  if (!st && e != cudaSuccess) st = cuda_fail(e, "dense coarse operator");
+  cudaFree(tmp);
+  if (!st) L.Q = h.Qmem;
+  return st;
+}
+
+// One fused Chebyshev step on one level (operator product and update in the
+// operator kernel's epilogue): reads d, writes dnext.
+int level_cheb(Mesh& m, const MgLevel& L, const float* d, float* dnext, float c1, float c2, const int* skip,
+               cudaStream_t s) {
+  ChebEpi epi;
+  epi.r = L.r;
+  epi.dinv = L.dinv;
+  epi.x = L.x;
+  epi.dnew = dnext;
+  epi.c1 = c1;
+  epi.c2 = c2;
+  const long long before = L.mesh->launches;
+  int st = launch_cheb_step(*L.mesh, d, epi, skip, s);
   if (L.mesh != &m) m.launches += L.mesh->launches - before;
   return st;
 }
@@ -591,16 +743,16 @@ int mg_setup(Mesh& m, const sipg_cg_opts& o, cudaStream_t s) {
     if (l + 1 < nl)
       for (int d = 0; d < 3; ++d) L.fac[d] = facs[l][d];
   }
-  // device memory: 6 FP32 vectors per level, 2 FP64 scratch vectors of level 0
+  // device memory: 7 FP32 vectors per level, 2 FP64 scratch vectors of level 0
   size_t bytes = 0;
   auto take = [&](size_t b) {
     size_t off = bytes;
     bytes += (b + 255) & ~(size_t)255;
     return off;
   };
-  std::vector<std::array<size_t, 6>> offs(nl);
+  std::vector<std::array<size_t, 7>> offs(nl);
   for (int l = 0; l < nl; ++l)
-    for (int j = 0; j < 6; ++j) offs[l][j] = take((size_t)h->lv[l].n * 4);
+    for (int j = 0; j < 7; ++j) offs[l][j] = take((size_t)h->lv[l].n * 4);
   const size_t o_a = take((size_t)h->lv[0].n * 8), o_b = take((size_t)h->lv[0].n * 8);
   cudaError_t e = cudaMalloc(&h->mem, bytes);
   if (e != cudaSuccess) {
@@ -617,6 +769,7 @@ int mg_setup(Mesh& m, const sipg_cg_opts& o, cudaStream_t s) {
     L.r = (float*)(base + offs[l][3]);
     L.d = (float*)(base + offs[l][4]);
     L.t = (float*)(base + offs[l][5]);
+    L.d2 = (float*)(base + offs[l][6]);
   }
   h->tmp_a = (double*)(base + o_a);
   h->tmp_b = (double*)(base + o_b);
@@ -666,6 +819,7 @@ int mg_setup(Mesh& m, const sipg_cg_opts& o, cudaStream_t s) {
       double lmin = 0.9 * rmin;
       if (!(lmin > 0.0) || lmin > lmax / 1.5) lmin = lmax / o.mg_range;  // guard against a poor estimate
       set_chebyshev(L, lmin, lmax, coarse_degree(lmin, lmax, o.mg_coarse_tol, o.mg_coarse_maxdeg));
+      if (L.n <= kDenseCoarseMax && (st = build_dense_coarse(m, *h, L, s))) return st;
     } else {
       const double lmax = 1.1 * rmax;
       set_chebyshev(L, lmax / o.mg_range, lmax, o.mg_degree);
@@ -709,22 +863,36 @@ int mg_vcycle(Mesh& m, const double* r64, double* z, const double* ap, const int
   // `final_out` writes z on the last step
   auto steps = [&](int l, bool final_out) -> int {
     MgLevel& L = h->lv[l];
+    float *dc = L.d, *dn = L.d2;
     for (int step = 1; step < L.degree; ++step) {
       int st2;
-      if ((st2 = level_apply(m, L, L.d, L.t, skip, s))) return st2;
-      if (final_out && step == L.degree - 1)
-        k_mg_step<false, true><<<kVB, kVT, 0, s>>>(skip, L.n, L.t, L.b, L.dinv, L.r, L.d, L.x, L.c1[step],
+      if (final_out && step == L.degree - 1) {
+        if ((st2 = level_apply(m, L, dc, L.t, skip, s))) return st2;
+        k_mg_step<false, true><<<kVB, kVT, 0, s>>>(skip, L.n, L.t, L.b, L.dinv, L.r, dc, L.x, L.c1[step],
                                                     L.c2[step], z, r64, ap, mean, part);
-      else
-        k_mg_step<false, false><<<kVB, kVT, 0, s>>>(skip, L.n, L.t, L.b, L.dinv, L.r, L.d, L.x, L.c1[step],
-                                                     L.c2[step], nullptr, nullptr, nullptr, nullptr, nullptr);
-      if ((st2 = vec_launched(m))) return st2;
+        if ((st2 = vec_launched(m))) return st2;
+      } else {
+        if ((st2 = level_cheb(m, L, dc, dn, L.c1[step], L.c2[step], skip, s))) return st2;
+        float* tmp = dc;
+        dc = dn;
+        dn = tmp;
+      }
     }
+    L.dlast = dc;
     return SIPG_OK;
   };
+  // coarsest level: the dense operator, else the Chebyshev iteration from zero
+  auto coarse_solve = [&](int l, bool final_out) -> int {
+    MgLevel& C = h->lv[l];
+    if (!C.Q) return steps(l, final_out);
+    const int rows = kVT / 32;
+    k_mg_dense<<<(unsigned)((C.n + rows - 1) / rows), kVT, (size_t)C.n * sizeof(float), s>>>(skip, (int)C.n, C.Q,
+                                                                                            C.b, C.x);
+    return vec_launched(m);
+  };
   if (nl == 1) {
-    if ((st = steps(0, true))) return st;
-    if (L0.degree == 1) {
+    if ((st = coarse_solve(0, true))) return st;
+    if (L0.Q || L0.degree == 1) {
       k_mg_out<<<kVB, kVT, 0, s>>>(skip, L0.n, L0.x, z, r64, ap, mean, part);
       if ((st = vec_launched(m))) return st;
     }
@@ -735,13 +903,12 @@ int mg_vcycle(Mesh& m, const double* r64, double* z, const double* ap, const int
     MgLevel& L = h->lv[l];
     MgLevel& C = h->lv[l + 1];
     if ((st = steps(l, false))) return st;
-    if ((st = level_apply(m, L, L.d, L.t, skip, s))) return st;
+    if ((st = level_apply(m, L, L.dlast, L.t, skip, s))) return st;
     const MgDims g = dims_of(L, C, p);
     if ((st = launch_restrict(p, g, skip, L.r, L.t, h->emb, C.b, C.r, C.d, C.x, C.dinv, C.inv_theta, s))) return st;
     m.launches++;
   }
-  // coarsest: Chebyshev from zero
-  if ((st = steps(nl - 1, false))) return st;
+  if ((st = coarse_solve(nl - 1, false))) return st;
   // up: prolongate and correct, post-smooth
   for (int l = nl - 2; l >= 0; --l) {
     MgLevel& L = h->lv[l];
@@ -755,8 +922,8 @@ int mg_vcycle(Mesh& m, const double* r64, double* z, const double* ap, const int
       k_mg_step<true, true><<<kVB, kVT, 0, s>>>(skip, L.n, L.t, L.b, L.dinv, L.r, L.d, L.x, 0.f, L.inv_theta, z, r64,
                                                  ap, mean, part);
     else
-      k_mg_step<true, false><<<kVB, kVT, 0, s>>>(skip, L.n, L.t, L.b, L.dinv, L.r, L.d, L.x, 0.f, L.inv_theta,
-                                                  nullptr, nullptr, nullptr, nullptr, nullptr);
+      k_mg_step<true, false><<<vec_grid(L.n), kVT, 0, s>>>(skip, L.n, L.t, L.b, L.dinv, L.r, L.d, L.x, 0.f,
+                                                            L.inv_theta, nullptr, nullptr, nullptr, nullptr, nullptr);
     if ((st = vec_launched(m))) return st;
     if ((st = steps(l, l == 0))) return st;
   }

@@ -34,22 +34,27 @@ constexpr int kMaxCellThreads = 256;  // block size limit of the cell kernels (r
 //   ts  = f (k+1)^2 t (this layer's share of tau_e),
 //   dTL, dTR = max(0, ts of the low / high neighbour layer - ts), so that the
 //   face penalty max(tau_e, tau_neighbour) of Eq. (tau) is tau_e + dT.
-// Table layout per layer, stride lstride(p):
-//   [M p*p][K p*p][Mi p*p][Kc p*p][dL p][dR p][dLh p][dRh p][h][t][ts][dTL][dTR][0][0][0]
-inline int lstride(int p) { return 4 * p * p + 4 * p + 8; }
+// Table layout per layer, stride lstride(p); every matrix block is padded to
+// lmat(p) = p*p rounded up to a multiple of 4 entries and every vector block to
+// lvec(p) = p rounded up to 4, so that each block starts 16-byte aligned (FP32
+// kernels read the blocks with 128-bit loads):
+//   [M][K][Mi][Kc] (lmat each) [dL][dR][dLh][dRh] (lvec each) [h][t][ts][dTL][dTR][0][0][0]
+inline int lmat(int p) { return (p * p + 3) / 4 * 4; }
+inline int lvec(int p) { return (p + 3) / 4 * 4; }
+inline int lstride(int p) { return 4 * lmat(p) + 4 * lvec(p) + 8; }
 inline int lay_M(int) { return 0; }
-inline int lay_K(int p) { return p * p; }
-inline int lay_Mi(int p) { return 2 * p * p; }
-inline int lay_Kc(int p) { return 3 * p * p; }
-inline int lay_dL(int p) { return 4 * p * p; }
-inline int lay_dR(int p) { return 4 * p * p + p; }
-inline int lay_dLh(int p) { return 4 * p * p + 2 * p; }
-inline int lay_dRh(int p) { return 4 * p * p + 3 * p; }
-inline int lay_h(int p) { return 4 * p * p + 4 * p; }
-inline int lay_t(int p) { return 4 * p * p + 4 * p + 1; }
-inline int lay_ts(int p) { return 4 * p * p + 4 * p + 2; }
-inline int lay_dTL(int p) { return 4 * p * p + 4 * p + 3; }
-inline int lay_dTR(int p) { return 4 * p * p + 4 * p + 4; }
+inline int lay_K(int p) { return lmat(p); }
+inline int lay_Mi(int p) { return 2 * lmat(p); }
+inline int lay_Kc(int p) { return 3 * lmat(p); }
+inline int lay_dL(int p) { return 4 * lmat(p); }
+inline int lay_dR(int p) { return 4 * lmat(p) + lvec(p); }
+inline int lay_dLh(int p) { return 4 * lmat(p) + 2 * lvec(p); }
+inline int lay_dRh(int p) { return 4 * lmat(p) + 3 * lvec(p); }
+inline int lay_h(int p) { return 4 * lmat(p) + 4 * lvec(p); }
+inline int lay_t(int p) { return 4 * lmat(p) + 4 * lvec(p) + 1; }
+inline int lay_ts(int p) { return 4 * lmat(p) + 4 * lvec(p) + 2; }
+inline int lay_dTL(int p) { return 4 * lmat(p) + 4 * lvec(p) + 3; }
+inline int lay_dTR(int p) { return 4 * lmat(p) + 4 * lvec(p) + 4; }
 
 // Geometry arguments shared by all cell kernels (passed by value).
 template <typename T>
@@ -121,6 +126,19 @@ struct DotSink {
   const int* skip = nullptr;
   int sums = 1;  // 0: only x.y is needed (sum y, sum x are left 0)
 };
+
+// Chebyshev-step epilogue of the FP32 Laplace operator (multigrid smoother):
+// with t = A d for the block's own unknowns, r -= t, dnew = c1 d + c2 dinv r,
+// x += dnew; t is not stored.  dnew must not alias d, which neighbouring blocks
+// still read.
+struct ChebEpi {
+  float* r = nullptr;
+  const float* dinv = nullptr;
+  float* x = nullptr;
+  float* dnew = nullptr;
+  float c1 = 0.f, c2 = 0.f;
+};
+int launch_cheb_step(const Mesh& m, const float* d, const ChebEpi& epi, const int* skip, cudaStream_t s);
 
 // Operator apply: y = mass_coef M x + nu (L x) [stiffness on/off]; nu_cell
 // replaces nu when not null.  Dot products go to `sink` (may be null); the
