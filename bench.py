@@ -496,7 +496,9 @@ def run_config(args):
         graph-captured CG with M^-1 and Jacobi);
     c4: Neumann-channel Poisson 48^3 k=5, FP32 Chebyshev(4) + FP64 flexible CG
         versus plain FP64 Jacobi CG;
-    c5: adjoint gradient on the 32^3 k=3 channel with per-cell viscosity."""
+    c5: adjoint gradient on the 32^3 k=3 channel with per-cell viscosity;
+    v3c: divergence, gradient, tau_D and the div-div local projection of the
+        pressure-projection step on the 32^3 k=4 channel."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -589,6 +591,36 @@ def run_config(args):
         out["backward_over_forward"] = (t_fb - t_f) / t_f
         out["finite_difference_estimate_s"] = 2 * m.ncell * t_f
         out["grad_norm"] = torch.linalg.norm(g).item()
+    elif args.workload == "v3c":
+        # the pressure-projection neighbours of the Poisson solve (variant V3c)
+        # on the 32^3 k=4 channel: divergence rhs, pressure gradient, tau_D
+        # and the div-div local projection; velocity = laminar profile + noise
+        from paper_1607_01323_gb300 import (apply_divdiv_f64, apply_divergence_f64, apply_gradient_f64,
+                                            project_divdiv_f64, tau_div_f64)
+        m = Mesh(w["n"], w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"], k=w["k"])
+        N = m.n_dofs
+        X = m.node_coordinates()
+        ux = (1 - X[:, 1] ** 2) + 0.1 * inputs.normal(0, "ux", N)
+        u = torch.tensor(np.concatenate([ux, 0.1 * inputs.normal(0, "uy", N), 0.1 * inputs.normal(0, "uz", N)]),
+                         device="cuda")
+        pr = torch.tensor(inputs.uniform(0, "p", N), device="cuda")
+        dt, gamma0 = 1e-3, 1.5
+        yd = torch.empty(N, dtype=torch.float64, device="cuda")
+        yg = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+        t_d, _ = _timed(lambda: [apply_divergence_f64(m, u, yd) for _ in range(20)], reps=3)
+        t_g, _ = _timed(lambda: [apply_gradient_f64(m, pr, yg) for _ in range(20)], reps=3)
+        tau = tau_div_f64(m, u, 1.0, dt)  # zeta_D = zeta* / CFL with zeta* = CFL = 1
+        t_t, _ = _timed(lambda: [tau_div_f64(m, u, 1.0, dt, tau) for _ in range(20)], reps=3)
+        rhs = apply_mass_f64(m, u) + (dt / gamma0) * apply_gradient_f64(m, pr)
+        t_p, (xp, iters) = _timed(lambda: project_divdiv_f64(m, tau, rhs, rtol=1e-8, maxit=500), reps=3)
+        res = apply_divdiv_f64(m, tau, xp) - rhs
+        out["dofs_per_component"] = N
+        out["divergence"] = {"ms": 1e3 * t_d / 20, "dofs_per_s": 3 * N / (t_d / 20)}
+        out["gradient"] = {"ms": 1e3 * t_g / 20, "dofs_per_s": 3 * N / (t_g / 20)}
+        out["tau_div"] = {"ms": 1e3 * t_t / 20, "mean": tau.mean().item(), "max": tau.max().item()}
+        out["divdiv_projection"] = {"s": t_p, "max_cell_iters": iters, "rtol": 1e-8,
+                                    "rel_residual": (torch.linalg.norm(res) / torch.linalg.norm(rhs)).item(),
+                                    "dofs_per_s": 3 * N / t_p}
     print(json.dumps(out))
 
 
@@ -607,7 +639,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--f64", default="double_float", choices=["native", "double_float"],
                     help="arithmetic of the FP64 operator (double_float: FP32 pairs on the FP32 pipes)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "v3c"],
                     help="c2 (default) is the bench step; c3-c5 print timings of the other configurations")
     args = ap.parse_args()
     if args.mode == "apply":

@@ -266,6 +266,40 @@ int sipg_mg_info(const sipg_mesh* mesh, int max_levels, int* nlevels, int* n_cel
  * n_dofs doubles).  Asynchronous on `stream`. */
 int sipg_mg_vcycle(sipg_mesh* mesh, const double* r, double* z, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Pressure-projection operators of the dual-splitting scheme, variant V3c
+ * (Sec. 3.3).  Velocities are 3 components u[d][cell][c][b][a] (d = x, y, z),
+ * pressures 1 component; DEVICE pointers, FP64, asynchronous on `stream`.
+ * The paper's factors gamma0/dt and dt/gamma0 are left to the caller.
+ * {{w}}^ND (Sec. 3.1) is the average on interior and periodic faces and the
+ * own trace on every boundary face (Dirichlet and Neumann sides alike). */
+
+/* y = D u, Eq. (av3): y_i = (grad phi_i, u)_e - (phi_i, {{u}}^ND . n)_de
+ * (u: 3 * n_dofs, y: n_dofs). */
+int sipg_apply_divergence_f64(const sipg_mesh* mesh, const double* u, double* y, void* stream);
+
+/* y = G p, Eq. (bv3): y_(d,i) = (d phi_i / d x_d, p)_e - (phi_i, {{p}}^ND n_d)_de
+ * (p: n_dofs, y: 3 * n_dofs).  On periodic faces G = -D^T. */
+int sipg_apply_gradient_f64(const sipg_mesh* mesh, const double* p, double* y, void* stream);
+
+/* tau[e] = zeta * |ubar_e| * V_e^(1/3) * dt, Eq. (tauD), with ubar_e the
+ * volume-averaged velocity of cell e (u: 3 * n_dofs; tau: ncell). */
+int sipg_tau_div_f64(const sipg_mesh* mesh, const double* u, double zeta, double dt, double* tau, void* stream);
+
+/* y = (M + tau_e B) u cell by cell, the operator of Eq. (div-div):
+ * B_(d,d') = (d phi_i / d x_d, d phi_j / d x_d')_e; tau: ncell values >= 0. */
+int sipg_apply_divdiv_f64(const sipg_mesh* mesh, const double* tau, const double* u, double* y, void* stream);
+
+/* Solve (M + tau_e B) x = rhs on every cell independently (the local
+ * projection of Eq. (div-div)) by CG preconditioned with the tensorial
+ * inverse mass matrix, one thread block per cell; x holds the initial guess
+ * on entry.  A cell stops when ||r|| <= rtol ||rhs_e|| or after maxit
+ * iterations.  Synchronous.  iters_out (HOST, may be NULL) receives the
+ * largest iteration count over the cells.  Returns SIPG_MAXITER if a cell did
+ * not converge, SIPG_BREAKDOWN on a non-positive curvature. */
+int sipg_project_divdiv_f64(sipg_mesh* mesh, const double* tau, const double* rhs, double* x, double rtol,
+                            int maxit, void* stream, int* iters_out);
+
 /* Size in bytes of the static workspace of sipg_cg_solve_noalloc (host output). */
 int sipg_cg_noalloc_capacity(long long* bytes);
 

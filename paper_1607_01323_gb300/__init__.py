@@ -16,7 +16,8 @@ from . import _lib as L
 
 __all__ = ["Mesh", "create_mesh", "apply_laplace_f64", "apply_laplace_f32", "apply_helmholtz_f64",
            "apply_helmholtz_f32", "apply_mass_f64", "apply_inverse_mass_f64", "diagonal_f64", "cg_solve",
-           "mg_setup", "mg_info", "mg_vcycle", "adjoint_grad_nu", "autotune", "CgResult", "SipgError"]
+           "mg_setup", "mg_info", "mg_vcycle", "apply_divergence_f64", "apply_gradient_f64", "tau_div_f64",
+           "apply_divdiv_f64", "project_divdiv_f64", "adjoint_grad_nu", "autotune", "CgResult", "SipgError"]
 
 SipgError = L.SipgError
 
@@ -290,6 +291,68 @@ def mg_vcycle(mesh, r, z=None, stream=None):
     L.check(L.lib().sipg_mg_vcycle(mesh.handle, _dev(r, torch.float64, "r"), _dev(z, torch.float64, "z"),
                                    _stream_ptr(stream)))
     return z
+
+
+def _vel(mesh, u, name):
+    torch = _torch()
+    if u.numel() != 3 * mesh.n_dofs:
+        raise ValueError("%s must hold 3 * n_dofs values (velocity components x, y, z)" % name)
+    return _dev(u, torch.float64, name)
+
+
+def apply_divergence_f64(mesh, u, y=None, stream=None):
+    """y = D u, the divergence of Eq. (av3) (u: 3 components, y: 1)."""
+    torch = _torch()
+    if y is None:
+        y = torch.empty(mesh.n_dofs, dtype=torch.float64, device=u.device)
+    L.check(L.lib().sipg_apply_divergence_f64(mesh.handle, _vel(mesh, u, "u"), _dev(y, torch.float64, "y"),
+                                              _stream_ptr(stream)))
+    return y
+
+
+def apply_gradient_f64(mesh, p, y=None, stream=None):
+    """y = G p, the gradient of Eq. (bv3) (p: 1 component, y: 3)."""
+    torch = _torch()
+    if p.numel() != mesh.n_dofs:
+        raise ValueError("p must hold n_dofs values")
+    if y is None:
+        y = torch.empty(3 * mesh.n_dofs, dtype=torch.float64, device=p.device)
+    L.check(L.lib().sipg_apply_gradient_f64(mesh.handle, _dev(p, torch.float64, "p"), _vel(mesh, y, "y"),
+                                            _stream_ptr(stream)))
+    return y
+
+
+def tau_div_f64(mesh, u, zeta, dt, out=None, stream=None):
+    """Per-cell div-div penalty tau_D of Eq. (tauD)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(mesh.ncell, dtype=torch.float64, device=u.device)
+    L.check(L.lib().sipg_tau_div_f64(mesh.handle, _vel(mesh, u, "u"), float(zeta), float(dt),
+                                     _dev(out, torch.float64, "tau"), _stream_ptr(stream)))
+    return out
+
+
+def apply_divdiv_f64(mesh, tau, u, y=None, stream=None):
+    """y = (M + tau_e B) u cell by cell, the operator of Eq. (div-div)."""
+    torch = _torch()
+    if y is None:
+        y = torch.empty_like(u)
+    L.check(L.lib().sipg_apply_divdiv_f64(mesh.handle, _dev(tau, torch.float64, "tau"), _vel(mesh, u, "u"),
+                                          _vel(mesh, y, "y"), _stream_ptr(stream)))
+    return y
+
+
+def project_divdiv_f64(mesh, tau, rhs, x=None, rtol=1e-12, maxit=200, stream=None):
+    """Solve the local projections (M + tau_e B) x = rhs (per-cell CG with the
+    inverse-mass preconditioner).  Returns (x, largest iteration count)."""
+    torch = _torch()
+    if x is None:
+        x = torch.zeros_like(rhs)
+    it = C.c_int()
+    L.check(L.lib().sipg_project_divdiv_f64(mesh.handle, _dev(tau, torch.float64, "tau"), _vel(mesh, rhs, "rhs"),
+                                            _vel(mesh, x, "x"), float(rtol), int(maxit), _stream_ptr(stream),
+                                            C.byref(it)))
+    return x, it.value
 
 
 def adjoint_grad_nu(mesh, nu_cell, u, lam, out=None, stream=None):

@@ -59,6 +59,12 @@ _SIGS = {
     "sipg_cg_solve_noalloc": [C.c_void_p, C.POINTER(CgOpts), C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                               C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "sipg_cg_noalloc_capacity": [C.POINTER(C.c_longlong)],
+    "sipg_apply_divergence_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "sipg_apply_gradient_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "sipg_tau_div_f64": [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p],
+    "sipg_apply_divdiv_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "sipg_project_divdiv_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,
+                                C.POINTER(C.c_int)],
     "sipg_mg_setup": [C.c_void_p, C.POINTER(CgOpts), C.c_void_p],
     "sipg_mg_info": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                      C.POINTER(C.c_int)],

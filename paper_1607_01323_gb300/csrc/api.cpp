@@ -37,6 +37,8 @@ Mesh::~Mesh() {
   for (int d = 0; d < 3; ++d)
     if (dtabdf[d]) cudaFree(dtabdf[d]);
   if (ws) cudaFree(ws);
+  if (dC64) cudaFree(dC64);
+  if (dC32) cudaFree(dC32);
   for (auto& pr : pending) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
@@ -488,6 +490,78 @@ int sipg_mg_vcycle(sipg_mesh* m, const double* r, double* z, void* stream) {
   if (!m->mg) return fail(SIPG_EINVAL, "no multigrid hierarchy set up on this mesh (sipg_mg_setup)");
   if ((st = set_device(*m))) return st;
   return mg_vcycle(*m, r, z, nullptr, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int sipg_apply_divergence_f64(const sipg_mesh* m, const double* u, double* y, void* stream) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!u || !y) return fail(SIPG_EINVAL, "NULL vector");
+  if (u == y) return fail(SIPG_EINVAL, "u and y must not overlap");
+  if ((st = set_device(const_cast<sipg_mesh&>(*m)))) return st;
+  return launch_divergence(*m, u, y, (cudaStream_t)stream);
+}
+
+int sipg_apply_gradient_f64(const sipg_mesh* m, const double* p, double* y, void* stream) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!p || !y) return fail(SIPG_EINVAL, "NULL vector");
+  if (p == y) return fail(SIPG_EINVAL, "p and y must not overlap");
+  if ((st = set_device(const_cast<sipg_mesh&>(*m)))) return st;
+  return launch_gradient(*m, p, y, (cudaStream_t)stream);
+}
+
+int sipg_tau_div_f64(const sipg_mesh* m, const double* u, double zeta, double dt, double* tau, void* stream) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!u || !tau) return fail(SIPG_EINVAL, "NULL vector");
+  if (!(zeta >= 0.0) || !(dt >= 0.0) || !std::isfinite(zeta) || !std::isfinite(dt))
+    return fail(SIPG_EINVAL, "zeta and dt must be finite and >= 0");
+  if ((st = set_device(const_cast<sipg_mesh&>(*m)))) return st;
+  return launch_tau_div(*m, u, zeta, dt, tau, (cudaStream_t)stream);
+}
+
+int sipg_apply_divdiv_f64(const sipg_mesh* m, const double* tau, const double* u, double* y, void* stream) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!tau || !u || !y) return fail(SIPG_EINVAL, "NULL vector");
+  if (u == y) return fail(SIPG_EINVAL, "u and y must not overlap");
+  if ((st = set_device(const_cast<sipg_mesh&>(*m)))) return st;
+  return launch_divdiv_apply(*m, tau, u, y, (cudaStream_t)stream);
+}
+
+int sipg_project_divdiv_f64(sipg_mesh* m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
+                            void* stream, int* iters_out) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!tau || !rhs || !x) return fail(SIPG_EINVAL, "NULL vector");
+  if (rhs == x) return fail(SIPG_EINVAL, "rhs and x must not overlap");
+  if (!(rtol >= 0.0) || maxit < 1) return fail(SIPG_EINVAL, "need rtol >= 0 and maxit >= 1");
+  if ((st = set_device(*m))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* status = nullptr;
+  cudaError_t e = cudaMalloc(&status, 2 * sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SIPG_ENOMEM, "cudaMalloc of the solve status failed");
+  }
+  e = cudaMemsetAsync(status, 0, 2 * sizeof(int), s);
+  if (e != cudaSuccess) {
+    cudaFree(status);
+    return cuda_fail(e, "clear solve status");
+  }
+  st = launch_divdiv_solve(*m, tau, rhs, x, rtol, maxit, status, s);
+  int h[2] = {0, 0};
+  if (!st) {
+    e = cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "read solve status");
+  }
+  cudaFree(status);
+  if (st) return st;
+  if (iters_out) *iters_out = h[1];
+  if (h[0] & 2) return fail(SIPG_BREAKDOWN, "local projection CG: non-positive curvature (tau < 0?)");
+  if (h[0] & 1) return fail(SIPG_MAXITER, "local projection CG: a cell did not converge within maxit");
+  return SIPG_OK;
 }
 
 int sipg_cg_noalloc_capacity(long long* bytes) {

@@ -1,0 +1,529 @@
+// Velocity-pressure coupling operators of the pressure-projection step,
+// variant V3c (Sec. 3.3), in FP64:
+//
+//   divergence, Eq. (av3):  y_i = (grad phi_i, u)_e - (phi_i, {{u}}^ND . n)_de
+//   gradient,   Eq. (bv3):  y_(d,i) = (d phi_i / dx_d, p)_e - (phi_i, {{p}}^ND n_d)_de
+//   div-div local projection, Eq. (div-div):  (M + tau_e B) w = rhs cell by cell,
+//       B_(d,d') = (d phi_i / dx_d, d phi_j / dx_d')_e,  tau_e of Eq. (tauD)
+//
+// ({{.}}^ND: the average on interior and periodic faces, the own trace on
+// boundary faces, Sec. 3.1.)  On the separable map every one of these
+// factorises into 1D matrices per direction and layer:
+//   (d phi_i / dx, phi_j) = C (x) M_y (x) M_z  with C[a][b] = int l_a' l_b, the
+//   same matrix for every layer (the Jacobian cancels);
+//   the face integral over an x-face is M_y (x) M_z applied to the face values;
+//   B_(x,x) = K_x (x) M_y (x) M_z,  B_(x,y) = C (x) C^T (x) M_z, ... .
+// So the divergence and gradient are, per direction d, the 1D operator
+// "C v plus the central-flux end terms" along d followed by the layer mass
+// matrices along the other two directions; the end terms need one value of
+// the neighbour's line (its value at the shared face).  Cells are processed
+// cell-centrically (each cell writes only its own outputs, no atomics).
+//
+// The local projection is solved per cell by CG preconditioned with the
+// tensorial inverse mass matrix (one thread block per cell, all vectors in
+// shared memory); Sec. 3.3 solves these local problems iteratively.
+#include <cmath>
+
+#include "apply.cuh"
+
+namespace sipg {
+
+namespace {
+
+constexpr int kDgThreads = 256;
+
+// 1D line operator of the divergence / gradient along one direction:
+// w = C v, then the central-flux end terms: the high face (n = +e_d) subtracts
+// {{v}} there, the low face (n = -e_d) adds it; {{v}} = (v_own + v_nb) / 2 on an
+// interior face, v_own on a boundary face.
+template <int P>
+__device__ __forceinline__ void line_divgrad(double (&w)[P], const double (&v)[P], const double* __restrict__ C,
+                                             int kL, double vL, int kR, double vR) {
+  matvec(w, C, v);
+  w[P - 1] -= kR == 0 ? 0.5 * (v[P - 1] + vR) : v[P - 1];
+  w[0] += kL == 0 ? 0.5 * (v[0] + vL) : v[0];
+}
+
+// MODE 0: divergence (3 components in, 1 out); MODE 1: gradient (1 in, 3 out).
+template <int P, int MODE>
+__global__ void __launch_bounds__(kDgThreads) divgrad_kernel(Geo<double> g, const double* __restrict__ C,
+                                                             const double* __restrict__ x, double* __restrict__ y,
+                                                             int cpb) {
+  using O = LayerOff<P>;
+  constexpr int P2 = P * P, P3 = P * P * P;
+  constexpr int NIN = MODE == 0 ? 3 : 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sv = reinterpret_cast<double*>(smraw);  // inputs [NIN][cpb][P3]
+  double* w1 = sv + (size_t)NIN * cpb * P3;        // [cpb][P3]
+  double* w2 = w1 + (size_t)cpb * P3;              // [cpb][P3]
+  double* acc = w2 + (size_t)cpb * P3;             // MODE 0: [cpb][P3]
+  const int cs = threadIdx.x / P2;
+  const int t = threadIdx.x - cs * P2;
+  const int ti = t % P, tj = t / P;
+  const long long cell0 = (long long)blockIdx.x * cpb;
+  const int e = (int)(cell0 + cs);
+  const bool active = cs < cpb && e < g.ncell;
+  const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
+  const long long N = (long long)g.ncell * P3;
+  for (int c = 0; c < NIN; ++c)
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x)
+      sv[(size_t)c * cpb * P3 + idx] = x[c * N + cell0 * P3 + idx];
+  if (MODE == 0)
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) acc[idx] = 0.0;
+  __syncthreads();
+  int id[3] = {0, 0, 0};
+  if (active) {
+    id[0] = e % g.n[0];
+    id[1] = (e / g.n[0]) % g.n[1];
+    id[2] = e / (g.n[0] * g.n[1]);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int d2 = d == 0 ? 1 : 0;  // the two other directions, d3 last
+    const int d3 = d == 2 ? 1 : 2;
+    const int comp = MODE == 0 ? d : 0;
+    if (active) {
+      int start, step;
+      line_geom<P>(d, ti, tj, start, step);
+      double v[P], w[P];
+      load_line<double, P>(v, sv + (size_t)comp * cpb * P3 + (size_t)cs * P3, start, step);
+      int nbL, nbR, kL, kR, jl, jr;
+      face_neighbor(g, d, 0, id[d], e, nbL, kL, jl);
+      face_neighbor(g, d, 1, id[d], e, nbR, kR, jr);
+      const double* xc = x + comp * N;
+      const double vL = kL == 0 ? xc[(long long)nbL * P3 + start + (P - 1) * step] : 0.0;
+      const double vR = kR == 0 ? xc[(long long)nbR * P3 + start] : 0.0;
+      line_divgrad<P>(w, v, C, kL, vL, kR, vR);
+      store_line<double, P>(w1 + (size_t)cs * P3, w, start, step);
+    }
+    __syncthreads();
+    if (active) {
+      int start, step;
+      line_geom<P>(d2, ti, tj, start, step);
+      double v[P], r[P];
+      load_line<double, P>(v, w1 + (size_t)cs * P3, start, step);
+      matvec(r, g.tab[d2] + id[d2] * O::stride + O::M, v);
+      store_line<double, P>(w2 + (size_t)cs * P3, r, start, step);
+    }
+    __syncthreads();
+    if (active) {
+      int start, step;
+      line_geom<P>(d3, ti, tj, start, step);
+      double v[P], r[P];
+      load_line<double, P>(v, w2 + (size_t)cs * P3, start, step);
+      matvec(r, g.tab[d3] + id[d3] * O::stride + O::M, v);
+      double* dst = (MODE == 0 ? acc : w1) + (size_t)cs * P3 + start;
+#pragma unroll
+      for (int a = 0; a < P; ++a) dst[a * step] = MODE == 0 ? dst[a * step] + r[a] : r[a];
+    }
+    __syncthreads();
+    if (MODE == 1) {
+      for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) y[d * N + cell0 * P3 + idx] = w1[idx];
+      __syncthreads();
+    }
+  }
+  if (MODE == 0)
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) y[cell0 * P3 + idx] = acc[idx];
+}
+
+// tau_D of Eq. (tauD), one warp per cell: the volume average of each velocity
+// component (the cell integral of phi_i is the product of the 1D mass
+// matrices' row sums), tau = zeta |ubar| V^(1/3) dt.
+template <int P>
+__global__ void tau_div_kernel(Geo<double> g, const double* __restrict__ u, double zeta, double dt,
+                               double* __restrict__ tau) {
+  using O = LayerOff<P>;
+  constexpr int P3 = P * P * P;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= g.ncell) return;
+  const int e = warp;
+  const int id[3] = {e % g.n[0], (e / g.n[0]) % g.n[1], e / (g.n[0] * g.n[1])};
+  const double* Mx = g.tab[0] + id[0] * O::stride + O::M;
+  const double* My = g.tab[1] + id[1] * O::stride + O::M;
+  const double* Mz = g.tab[2] + id[2] * O::stride + O::M;
+  const long long N = (long long)g.ncell * P3;
+  double s[3] = {0.0, 0.0, 0.0}, vol = 0.0;
+  for (int i = lane; i < P3; i += 32) {
+    const int a = i % P, b = (i / P) % P, c = i / (P * P);
+    double mx = 0.0, my = 0.0, mz = 0.0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      mx += Mx[a * P + q];
+      my += My[b * P + q];
+      mz += Mz[c * P + q];
+    }
+    const double m = mx * my * mz;
+    vol += m;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s[d] += m * u[d * N + (long long)e * P3 + i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vol += __shfl_down_sync(0xffffffffu, vol, o);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s[d] += __shfl_down_sync(0xffffffffu, s[d], o);
+  }
+  if (lane == 0) {
+    const double ux = s[0] / vol, uy = s[1] / vol, uz = s[2] / vol;
+    tau[e] = zeta * sqrt(ux * ux + uy * uy + uz * uz) * cbrt(vol) * dt;
+  }
+}
+
+// ------------------------------------------------------ one-cell operators
+// One thread block per cell; thread t < P^2 owns line t of each phase.
+struct CellCtx {
+  const double* L[3];  // the cell's layer table per direction
+  const double* C;     // C (shared memory)
+  const double* Ct;    // C^T (shared memory)
+  int t;
+  bool active;         // t < P^2
+};
+
+// out (op)= scale * (A_x (x) A_y (x) A_z) in, where direction r's matrix is
+// A_r + c_r B_r (B_r may be null); in, out: [P3]; t1, t2: [P3] scratch.
+// op: 0 store, 1 add.
+template <int P>
+__device__ void cell_chain(const CellCtx& cc, const double* const (&A)[3], const double* const (&B)[3],
+                           const double (&cB)[3], const double* in, double* out, double* t1, double* t2, int op,
+                           double scale) {
+  const int ti = cc.t % P, tj = cc.t / P;
+  const double* src[3] = {in, t1, t2};
+  double* dst[3] = {t1, t2, out};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if (cc.active) {
+      int start, step;
+      line_geom<P>(r, ti, tj, start, step);
+      double v[P], w[P];
+      load_line<double, P>(v, src[r], start, step);
+      matvec(w, A[r], v);
+      if (B[r]) {
+        double w2[P];
+        matvec(w2, B[r], v);
+#pragma unroll
+        for (int a = 0; a < P; ++a) w[a] = fma(cB[r], w2[a], w[a]);
+      }
+      if (r < 2) {
+        store_line<double, P>(dst[r], w, start, step);
+      } else {
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+          const double val = scale * w[a];
+          dst[r][start + a * step] = op ? dst[r][start + a * step] + val : val;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y = (M + tau B) u on one cell: u, y: [3][P3]
+template <int P>
+__device__ void divdiv_cell(const CellCtx& cc, double tau, const double* u, double* y, double* t1, double* t2) {
+  using O = LayerOff<P>;
+  constexpr int P3 = P * P * P;
+  const double* Mr[3] = {cc.L[0] + O::M, cc.L[1] + O::M, cc.L[2] + O::M};
+  const double* Kr[3] = {cc.L[0] + O::K, cc.L[1] + O::K, cc.L[2] + O::K};
+  for (int d = 0; d < 3; ++d) {
+    // diagonal block: (M_d + tau K_d) along d, M along the others
+    {
+      const double* A[3] = {Mr[0], Mr[1], Mr[2]};
+      const double* B[3] = {nullptr, nullptr, nullptr};
+      double cB[3] = {0.0, 0.0, 0.0};
+      B[d] = Kr[d];
+      cB[d] = tau;
+      cell_chain<P>(cc, A, B, cB, u + d * P3, y + d * P3, t1, t2, 0, 1.0);
+    }
+    // off-diagonal blocks: C along d (test derivative), C^T along d' (trial derivative)
+    for (int dp = 0; dp < 3; ++dp) {
+      if (dp == d) continue;
+      const double* A[3] = {Mr[0], Mr[1], Mr[2]};
+      A[d] = cc.C;
+      A[dp] = cc.Ct;
+      const double* B[3] = {nullptr, nullptr, nullptr};
+      const double cB[3] = {0.0, 0.0, 0.0};
+      cell_chain<P>(cc, A, B, cB, u + dp * P3, y + d * P3, t1, t2, 1, tau);
+    }
+  }
+}
+
+// z = M^-1 r per component (tensorial inverse mass, Sec. 5)
+template <int P>
+__device__ void invmass_cell(const CellCtx& cc, const double* r, double* z, double* t1, double* t2) {
+  using O = LayerOff<P>;
+  constexpr int P3 = P * P * P;
+  const double* A[3] = {cc.L[0] + O::Mi, cc.L[1] + O::Mi, cc.L[2] + O::Mi};
+  const double* B[3] = {nullptr, nullptr, nullptr};
+  const double cB[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < 3; ++d) cell_chain<P>(cc, A, B, cB, r + d * P3, z + d * P3, t1, t2, 0, 1.0);
+}
+
+// sum of v over the block (blockDim <= 1024), result broadcast to all threads
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) s += red[w];
+  return s;
+}
+
+template <int P>
+__device__ CellCtx cell_ctx(const Geo<double>& g, int e, const double* C, const double* Ct) {
+  using O = LayerOff<P>;
+  CellCtx cc;
+  const int id[3] = {e % g.n[0], (e / g.n[0]) % g.n[1], e / (g.n[0] * g.n[1])};
+  for (int d = 0; d < 3; ++d) cc.L[d] = g.tab[d] + id[d] * O::stride;
+  cc.C = C;
+  cc.Ct = Ct;
+  cc.t = threadIdx.x;
+  cc.active = threadIdx.x < P * P;
+  return cc;
+}
+
+// stage C and C^T in shared memory
+template <int P>
+__device__ void stage_c(const double* __restrict__ Cg, double* C, double* Ct) {
+  for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+    const int a = i / P, b = i % P;
+    C[i] = Cg[i];
+    Ct[b * P + a] = Cg[i];
+  }
+}
+
+template <int P>
+__global__ void divdiv_apply_kernel(Geo<double> g, const double* __restrict__ Cg, const double* __restrict__ tau,
+                                    const double* __restrict__ u, double* __restrict__ y) {
+  constexpr int P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* su = reinterpret_cast<double*>(smraw);  // [3][P3]
+  double* sy = su + 3 * P3;                        // [3][P3]
+  double* t1 = sy + 3 * P3;
+  double* t2 = t1 + P3;
+  double* C = t2 + P3;
+  double* Ct = C + P * P;
+  const int e = blockIdx.x;
+  const long long N = (long long)g.ncell * P3;
+  for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x) su[i] = u[(i / P3) * N + (long long)e * P3 + i % P3];
+  stage_c<P>(Cg, C, Ct);
+  __syncthreads();
+  const CellCtx cc = cell_ctx<P>(g, e, C, Ct);
+  divdiv_cell<P>(cc, tau[e], su, sy, t1, t2);
+  for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x) y[(i / P3) * N + (long long)e * P3 + i % P3] = sy[i];
+}
+
+// Per-cell CG on (M + tau B) x = rhs with z = M^-1 r; x holds the initial
+// guess.  status[0] |= 1 if a cell stops at maxit, |= 2 on breakdown;
+// status[1] = max iterations over the cells.
+template <int P>
+__global__ void divdiv_solve_kernel(Geo<double> g, const double* __restrict__ Cg, const double* __restrict__ tau,
+                                    const double* __restrict__ rhs, double* __restrict__ x, double rtol, int maxit,
+                                    int* __restrict__ status) {
+  constexpr int P3 = P * P * P, V = 3 * P3;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* sx = reinterpret_cast<double*>(smraw);
+  double* sr = sx + V;
+  double* sz = sr + V;
+  double* sp = sz + V;
+  double* sq = sp + V;
+  double* t1 = sq + V;
+  double* t2 = t1 + P3;
+  double* C = t2 + P3;
+  double* Ct = C + P * P;
+  double* red = Ct + P * P;  // 32
+  const int e = blockIdx.x;
+  const long long N = (long long)g.ncell * P3;
+  double bb = 0.0;
+  for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    const long long gi = (i / P3) * N + (long long)e * P3 + i % P3;
+    sx[i] = x[gi];
+    sr[i] = rhs[gi];
+    bb += sr[i] * sr[i];
+  }
+  stage_c<P>(Cg, C, Ct);
+  __syncthreads();
+  bb = block_sum(bb, red);
+  const CellCtx cc = cell_ctx<P>(g, e, C, Ct);
+  const double te = tau[e];
+  // r = rhs - A x
+  divdiv_cell<P>(cc, te, sx, sq, t1, t2);
+  double rr = 0.0;
+  for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    sr[i] -= sq[i];
+    rr += sr[i] * sr[i];
+  }
+  __syncthreads();
+  rr = block_sum(rr, red);
+  invmass_cell<P>(cc, sr, sz, t1, t2);
+  double rz = 0.0;
+  for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    sp[i] = sz[i];
+    rz += sr[i] * sz[i];
+  }
+  __syncthreads();
+  rz = block_sum(rz, red);
+  const double tol2 = rtol * rtol * bb;
+  int it = 0;
+  bool broke = false;
+  while (rr > tol2 && it < maxit) {
+    divdiv_cell<P>(cc, te, sp, sq, t1, t2);
+    double pq = 0.0;
+    for (int i = threadIdx.x; i < V; i += blockDim.x) pq += sp[i] * sq[i];
+    pq = block_sum(pq, red);
+    if (!(pq > 0.0)) {
+      broke = true;
+      break;
+    }
+    const double alpha = rz / pq;
+    rr = 0.0;
+    for (int i = threadIdx.x; i < V; i += blockDim.x) {
+      sx[i] = fma(alpha, sp[i], sx[i]);
+      sr[i] = fma(-alpha, sq[i], sr[i]);
+      rr += sr[i] * sr[i];
+    }
+    __syncthreads();
+    rr = block_sum(rr, red);
+    invmass_cell<P>(cc, sr, sz, t1, t2);
+    double rzn = 0.0;
+    for (int i = threadIdx.x; i < V; i += blockDim.x) rzn += sr[i] * sz[i];
+    rzn = block_sum(rzn, red);
+    const double beta = rzn / rz;
+    rz = rzn;
+    for (int i = threadIdx.x; i < V; i += blockDim.x) sp[i] = fma(beta, sp[i], sz[i]);
+    __syncthreads();
+    ++it;
+  }
+  for (int i = threadIdx.x; i < V; i += blockDim.x) x[(i / P3) * N + (long long)e * P3 + i % P3] = sx[i];
+  if (threadIdx.x == 0) {
+    if (broke) atomicOr(status, 2);
+    else if (rr > tol2) atomicOr(status, 1);
+    atomicMax(status + 1, it);
+  }
+}
+
+int cell_threads(int p) { return (p * p + 31) / 32 * 32; }
+
+int proj_cpb(int p) {
+  const int c = kDgThreads / (p * p);
+  return c < 1 ? 1 : c;
+}
+
+template <int P>
+int launch_divgrad_p(const Mesh& m, const double* x, double* y, int mode, cudaStream_t s) {
+  const int cpb = proj_cpb(P);
+  const int threads = (cpb * P * P + 31) / 32 * 32;
+  const int nbuf = mode == 0 ? 3 + 3 : 1 + 2;
+  const size_t smem = (size_t)nbuf * cpb * P * P * P * sizeof(double);
+  const unsigned blocks = (unsigned)((m.ncell + cpb - 1) / cpb);
+  const Geo<double> g = make_geo<double>(m);
+  cudaError_t e;
+  if (mode == 0) {
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(divgrad_kernel<P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute(divergence)");
+    divgrad_kernel<P, 0><<<blocks, threads, smem, s>>>(g, m.dC64, x, y, cpb);
+  } else {
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(divgrad_kernel<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute(gradient)");
+    divgrad_kernel<P, 1><<<blocks, threads, smem, s>>>(g, m.dC64, x, y, cpb);
+  }
+  const_cast<Mesh&>(m).launches++;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "divergence / gradient launch");
+}
+
+template <int P>
+int launch_tau_p(const Mesh& m, const double* u, double zeta, double dt, double* tau, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((m.ncell * 32 + threads - 1) / threads);
+  tau_div_kernel<P><<<blocks, threads, 0, s>>>(make_geo<double>(m), u, zeta, dt, tau);
+  const_cast<Mesh&>(m).launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "tau_D launch");
+}
+
+template <int P>
+int launch_divdiv_apply_p(const Mesh& m, const double* tau, const double* u, double* y, cudaStream_t s) {
+  constexpr int P3 = P * P * P;
+  const size_t smem = (size_t)(8 * P3 + 2 * P * P) * sizeof(double);
+  cudaError_t e;
+  if (smem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(divdiv_apply_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+          cudaSuccess)
+    return cuda_fail(e, "cudaFuncSetAttribute(div-div apply)");
+  divdiv_apply_kernel<P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<double>(m), m.dC64, tau, u, y);
+  const_cast<Mesh&>(m).launches++;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "div-div apply launch");
+}
+
+template <int P>
+int launch_divdiv_solve_p(const Mesh& m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
+                          int* status, cudaStream_t s) {
+  constexpr int P3 = P * P * P;
+  const size_t smem = (size_t)(15 * P3 + 2 * P3 + 2 * P * P + 32) * sizeof(double);
+  cudaError_t e;
+  if (smem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(divdiv_solve_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+          cudaSuccess)
+    return cuda_fail(e, "cudaFuncSetAttribute(div-div solve)");
+  divdiv_solve_kernel<P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<double>(m), m.dC64, tau, rhs, x,
+                                                                          rtol, maxit, status);
+  const_cast<Mesh&>(m).launches++;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "div-div solve launch");
+}
+
+}  // namespace
+
+#define SIPG_PROJ_DISPATCH(CALL)                               \
+  switch (m.p) {                                               \
+    case 2: return CALL(2);                                    \
+    case 3: return CALL(3);                                    \
+    case 4: return CALL(4);                                    \
+    case 5: return CALL(5);                                    \
+    case 6: return CALL(6);                                    \
+    case 7: return CALL(7);                                    \
+    case 8: return CALL(8);                                    \
+    default: return fail(SIPG_EINVAL, "unsupported degree");  \
+  }
+
+int launch_divergence(const Mesh& m, const double* u, double* y, cudaStream_t s) {
+#define CALL(P) launch_divgrad_p<P>(m, u, y, 0, s)
+  SIPG_PROJ_DISPATCH(CALL)
+#undef CALL
+}
+
+int launch_gradient(const Mesh& m, const double* p, double* y, cudaStream_t s) {
+#define CALL(P) launch_divgrad_p<P>(m, p, y, 1, s)
+  SIPG_PROJ_DISPATCH(CALL)
+#undef CALL
+}
+
+int launch_tau_div(const Mesh& m, const double* u, double zeta, double dt, double* tau, cudaStream_t s) {
+#define CALL(P) launch_tau_p<P>(m, u, zeta, dt, tau, s)
+  SIPG_PROJ_DISPATCH(CALL)
+#undef CALL
+}
+
+int launch_divdiv_apply(const Mesh& m, const double* tau, const double* u, double* y, cudaStream_t s) {
+#define CALL(P) launch_divdiv_apply_p<P>(m, tau, u, y, s)
+  SIPG_PROJ_DISPATCH(CALL)
+#undef CALL
+}
+
+int launch_divdiv_solve(const Mesh& m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
+                        int* status, cudaStream_t s) {
+#define CALL(P) launch_divdiv_solve_p<P>(m, tau, rhs, x, rtol, maxit, status, s)
+  SIPG_PROJ_DISPATCH(CALL)
+#undef CALL
+}
+
+#undef SIPG_PROJ_DISPATCH
+
+}  // namespace sipg

@@ -77,6 +77,12 @@ struct Mesh {
   double* dtab64[3] = {nullptr, nullptr, nullptr};
   float* dtab32[3] = {nullptr, nullptr, nullptr};
   dfl* dtabdf[3] = {nullptr, nullptr, nullptr};  // double-float copies (hi, lo)
+  // reference derivative-mass matrix C[a][b] = int_0^1 l_a'(s) l_b(s) ds (Gauss
+  // k+1, exact); the same for every layer: the map's Jacobian cancels in
+  // (d phi_a / dx, phi_b) on a separable map
+  std::vector<double> hC;
+  double* dC64 = nullptr;
+  float* dC32 = nullptr;
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
   int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
@@ -162,6 +168,17 @@ int launch_adjoint(const Mesh& m, const double* nu_cell, const double* u, const 
 
 int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s, int* iters,
              double* relres);
+
+// Pressure-projection operators (projection.cu, FP64): divergence of Eq. (av3)
+// (3 components in, 1 out), gradient of Eq. (bv3) (1 in, 3 out), tau_D of
+// Eq. (tauD), the div-div operator of Eq. (div-div) and its batched per-cell
+// CG solve with the inverse-mass preconditioner.
+int launch_divergence(const Mesh& m, const double* u, double* y, cudaStream_t s);
+int launch_gradient(const Mesh& m, const double* p, double* y, cudaStream_t s);
+int launch_tau_div(const Mesh& m, const double* u, double zeta, double dt, double* tau, cudaStream_t s);
+int launch_divdiv_apply(const Mesh& m, const double* tau, const double* u, double* y, cudaStream_t s);
+int launch_divdiv_solve(const Mesh& m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
+                        int* status_dev, cudaStream_t s);
 
 int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s,
                      int* iters, double* relres);

@@ -209,6 +209,14 @@ int build_tables(Mesh& m) {
   }
   lagrange_eval(zn, 0.0, v, d0);
   lagrange_eval(zn, 1.0, v, d1);
+  // C[a][b] = sum_q w_q l_a'(z_q) l_b(z_q)
+  m.hC.assign((size_t)p * p, 0.0);
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b) {
+      long double sc = 0.0L;
+      for (int q = 0; q < p; ++q) sc += (long double)wq[q] * D[q * p + a] * S[q * p + b];
+      m.hC[a * p + b] = (double)sc;
+    }
   const int st = lstride(p);
   for (int dir = 0; dir < 3; ++dir) {
     const int n = m.desc.n[dir];
@@ -285,6 +293,20 @@ int build_tables(Mesh& m) {
     }
   }
   // upload (double, float and double-float copies)
+  {
+    if (m.dC64) cudaFree(m.dC64);
+    if (m.dC32) cudaFree(m.dC32);
+    m.dC64 = nullptr;
+    m.dC32 = nullptr;
+    std::vector<float> cf(m.hC.begin(), m.hC.end());
+    cudaError_t e = cudaMalloc(&m.dC64, m.hC.size() * sizeof(double));
+    if (e != cudaSuccess) return fail(SIPG_ENOMEM, "cudaMalloc of the derivative-mass table failed");
+    e = cudaMalloc(&m.dC32, cf.size() * sizeof(float));
+    if (e != cudaSuccess) return fail(SIPG_ENOMEM, "cudaMalloc of the derivative-mass table failed");
+    e = cudaMemcpy(m.dC64, m.hC.data(), m.hC.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m.dC32, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload derivative-mass table");
+  }
   for (int dir = 0; dir < 3; ++dir) {
     if (m.dtab64[dir]) cudaFree(m.dtab64[dir]);
     if (m.dtab32[dir]) cudaFree(m.dtab32[dir]);
