@@ -599,10 +599,11 @@ struct UniformMinBlocks {
                                : (std::is_same<T, float>::value ? (P <= 6 ? 4 : (P == 7 ? 3 : 2)) : (P <= 6 ? 2 : 1));
 };
 
-// Shared memory of apply_uniform_kernel: own cells and two line-result buffers.
+// Shared memory of apply_uniform_kernel: own cells (kept to the end for the
+// dot products and the Chebyshev epilogue) and three line-result buffers.
 template <typename T, int P>
 __host__ __device__ constexpr size_t uniform_smem_bytes(int cpb) {
-  return (size_t)3 * cpb * P * P * P * sizeof(T);
+  return (size_t)4 * cpb * P * P * P * sizeof(T);
 }
 
 // CHEB (FP32 only): instead of storing y = A x, apply one Chebyshev step of the
@@ -620,6 +621,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   T* su = reinterpret_cast<T*>(smem_raw);
   T* s1 = su + cpb * P3;
   T* s2 = s1 + cpb * P3;
+  T* s3 = s2 + cpb * P3;
   const int cs = threadIdx.x / P2;
   const int t = threadIdx.x - cs * P2;
   const int ti = t % P, tj = t / P;
@@ -637,6 +639,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   T* us = su + cs * P3;
   T* w1 = s1 + cs * P3;
   T* w2 = s2 + cs * P3;
+  T* w3 = s3 + cs * P3;
   int id[3] = {0, 0, 0};
   T tau_e = T(0);
   if (active) {
@@ -710,7 +713,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
 #pragma unroll
       for (int a = 0; a < P; ++a) w[a] = fma(mass_rel, mu[a], w[a]);
     }
-    store_line<T, P>(us, w, start, step);
+    store_line<T, P>(w3, w, start, step);
   }
   __syncthreads();
   if (active) {
@@ -721,7 +724,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     load_line<T, P>(v, w1, start, step);
     matvec(r, My, v);
     store_line<T, P>(w1, r, start, step);
-    load_line<T, P>(v, us, start, step);
+    load_line<T, P>(v, w3, start, step);
     matvec(r, My, v);
     load_line<T, P>(v, w2, start, step);
 #pragma unroll
@@ -740,9 +743,9 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     load_line<T, P>(r1, w1, start, step);
     if constexpr (CHEB) {
       static_assert(std::is_same<T, float>::value && std::is_same<S, float>::value, "FP32 only");
-      // t = A d for this x-line; d (the input) is read again (cached)
+      // t = A d for this x-line; d (the input) from the staged cell
       T dold[P];
-      load_line_global_cvt<T, S, P>(dold, xc + (long long)e * P3, start, step);
+      load_line<T, P>(dold, us, start, step);
       const long long o = cbase + (long long)e * P3 + start;
 #pragma unroll
       for (int a = 0; a < P; ++a) {
@@ -765,9 +768,9 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     }
     if (!CHEB && dots) {
       // line sums in the compute type, one conversion per line; the x-line of
-      // the input is read again (cached) instead of being held in registers
+      // the input from the staged cell
       T ux[P];
-      load_line_global_cvt<T, S, P>(ux, xc + (long long)e * P3, start, step);
+      load_line<T, P>(ux, us, start, step);
       T sxy(0), sy(0), sx(0);
 #pragma unroll
       for (int a = 0; a < P; ++a) sxy = fma(out[a], ux[a], sxy);

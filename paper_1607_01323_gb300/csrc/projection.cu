@@ -325,9 +325,9 @@ __global__ void divdiv_solve_kernel(Geo<double> g, const double* __restrict__ Cg
   extern __shared__ __align__(16) unsigned char smraw[];
   double* sx = reinterpret_cast<double*>(smraw);
   double* sr = sx + V;
-  double* sz = sr + V;
-  double* sp = sz + V;
-  double* sq = sp + V;
+  double* sp = sr + V;
+  double* sq = sp + V;  // A p, and after the updates z = M^-1 r (one buffer)
+  double* sz = sq;
   double* t1 = sq + V;
   double* t2 = t1 + P3;
   double* C = t2 + P3;
@@ -466,7 +466,7 @@ template <int P>
 int launch_divdiv_solve_p(const Mesh& m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
                           int* status, cudaStream_t s) {
   constexpr int P3 = P * P * P;
-  const size_t smem = (size_t)(15 * P3 + 2 * P3 + 2 * P * P + 32) * sizeof(double);
+  const size_t smem = (size_t)(12 * P3 + 2 * P3 + 2 * P * P + 32) * sizeof(double);
   cudaError_t e;
   if (smem > 48 * 1024 &&
       (e = cudaFuncSetAttribute(divdiv_solve_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
