@@ -359,11 +359,19 @@ __device__ __forceinline__ void sink_dots(const DotSink& s, double a, double b, 
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // several loads in flight per thread (this tail runs on one block only);
+  // without the zero-mean sums only x.y is read
   double x = 0.0, y = 0.0, z = 0.0;
-  for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
-    x += __ldcg(s.partials + 3 * i);
-    y += __ldcg(s.partials + 3 * i + 1);
-    z += __ldcg(s.partials + 3 * i + 2);
+  if (s.sums) {
+#pragma unroll 4
+    for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) {
+      x += __ldcg(s.partials + 3 * i);
+      y += __ldcg(s.partials + 3 * i + 1);
+      z += __ldcg(s.partials + 3 * i + 2);
+    }
+  } else {
+#pragma unroll 8
+    for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) x += __ldcg(s.partials + 3 * i);
   }
   double t[3];
   block_reduce3(x, y, z, t);  // thread 0 holds the totals

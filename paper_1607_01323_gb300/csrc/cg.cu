@@ -300,6 +300,7 @@ __global__ void k_update(Scalars* sc, long long n, double* __restrict__ x, doubl
   if (!last) return;
   __threadfence();
   double a = 0.0, b = 0.0, c = 0.0;
+#pragma unroll 4
   for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
     a += __ldcg(part + 3 * i);
     b += __ldcg(part + 3 * i + 1);
