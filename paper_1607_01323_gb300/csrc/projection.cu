@@ -134,26 +134,29 @@ __global__ void tau_div_kernel(Geo<double> g, const double* __restrict__ u, doub
                                double* __restrict__ tau) {
   using O = LayerOff<P>;
   constexpr int P3 = P * P * P;
+  __shared__ double rs[8][3][P];  // row sums per warp of the block (blockDim = 256)
+  const int wib = threadIdx.x >> 5;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= g.ncell) return;
-  const int e = warp;
+  const bool valid = warp < g.ncell;
+  const int e = valid ? warp : 0;
   const int id[3] = {e % g.n[0], (e / g.n[0]) % g.n[1], e / (g.n[0] * g.n[1])};
-  const double* Mx = g.tab[0] + id[0] * O::stride + O::M;
-  const double* My = g.tab[1] + id[1] * O::stride + O::M;
-  const double* Mz = g.tab[2] + id[2] * O::stride + O::M;
+  if (lane < 3 * P) {
+    const int d = lane / P, a = lane % P;
+    const double* Md = (d == 0 ? g.tab[0] + id[0] * O::stride : (d == 1 ? g.tab[1] + id[1] * O::stride
+                                                                       : g.tab[2] + id[2] * O::stride)) + O::M;
+    double r = 0.0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) r += Md[a * P + q];
+    rs[wib][d][a] = r;
+  }
+  __syncwarp();
+  if (!valid) return;
   const long long N = (long long)g.ncell * P3;
   double s[3] = {0.0, 0.0, 0.0}, vol = 0.0;
   for (int i = lane; i < P3; i += 32) {
     const int a = i % P, b = (i / P) % P, c = i / (P * P);
-    double mx = 0.0, my = 0.0, mz = 0.0;
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      mx += Mx[a * P + q];
-      my += My[b * P + q];
-      mz += Mz[c * P + q];
-    }
-    const double m = mx * my * mz;
+    const double m = rs[wib][0][a] * rs[wib][1][b] * rs[wib][2][c];
     vol += m;
 #pragma unroll
     for (int d = 0; d < 3; ++d) s[d] += m * u[d * N + (long long)e * P3 + i];
