@@ -493,7 +493,8 @@ def run_config(args):
     """Timings of the other workload configurations (one JSON line each):
     c1: the 4^3 periodic unit cube at k=3 (operator apply only);
     c3: 3-component viscous Helmholtz on the 64^3 k=3 channel (apply, autotune,
-        graph-captured CG with M^-1 and Jacobi);
+        graph-captured CG with M^-1 and Jacobi), in the Laplace form of the
+        configuration and in the paper's divergence form (coupled components);
     c4: Neumann-channel Poisson 48^3 k=5, FP32 Chebyshev(4) + FP64 flexible CG
         versus plain FP64 Jacobi CG;
     c5: adjoint gradient on the 32^3 k=3 channel with per-cell viscosity;
@@ -540,6 +541,15 @@ def run_config(args):
                 out["solve_%s_%s" % (pc, "graph" if graph else "loop")] = {
                     "s": t, "iters": res.iters, "relres": res.relres,
                     "dof_applies_per_s": 3 * N * (res.iters + 1) / t}
+        # the paper's divergence-form viscous operator (eps(u), coupled
+        # components) on the same mesh and input, and its M^-1-preconditioned CG
+        from paper_1607_01323_gb300 import apply_viscous_f64
+        t_v, _ = _timed(lambda: apply_viscous_f64(m, u, cm, nu, y=y), reps=5)
+        out["apply_viscous_div_form"] = {"ms": 1e3 * t_v, "dofs": 3 * N, "dofs_per_s": 3 * N / t_v}
+        t, (x, res) = _timed(lambda: cg_solve(m, rhs, torch.zeros_like(rhs), op="viscous", mass_coef=cm, nu=nu,
+                                              precond="invmass", rtol=1e-10), reps=3)
+        out["solve_viscous_div_form_invmass_graph"] = {"s": t, "iters": res.iters, "relres": res.relres,
+                                                       "dof_applies_per_s": 3 * N * (res.iters + 1) / t}
     elif args.workload == "c4":
         m = Mesh((48, 48, 48), w["lo"], w["hi"], ("periodic", "neumann", "periodic"),
                  ("periodic", "neumann", "periodic"), mapping="channel", gamma=1.8, k=5)

@@ -59,7 +59,10 @@ typedef enum {
 
 typedef enum { SIPG_BC_PERIODIC = 0, SIPG_BC_DIRICHLET = 1, SIPG_BC_NEUMANN = 2 } sipg_bc;
 typedef enum { SIPG_MAP_AFFINE = 0, SIPG_MAP_CHANNEL_TANH = 1, SIPG_MAP_CHANNEL_LINEAR = 2 } sipg_map;
-typedef enum { SIPG_OP_LAPLACE = 0, SIPG_OP_HELMHOLTZ = 1 } sipg_op;
+/* SIPG_OP_VISCOUS: mass_coef M + the divergence-form viscous operator of
+ * sipg_apply_viscous_f64 (3 coupled components; CG with SIPG_PC_NONE or
+ * SIPG_PC_INVMASS). */
+typedef enum { SIPG_OP_LAPLACE = 0, SIPG_OP_HELMHOLTZ = 1, SIPG_OP_VISCOUS = 2 } sipg_op;
 typedef enum { SIPG_F64_NATIVE = 0, SIPG_F64_DOUBLE_FLOAT = 1 } sipg_f64_arith;
 typedef enum {
   SIPG_PC_NONE = 0,
@@ -299,6 +302,19 @@ int sipg_apply_divdiv_f64(const sipg_mesh* mesh, const double* tau, const double
  * not converge, SIPG_BREAKDOWN on a non-positive curvature. */
 int sipg_project_divdiv_f64(sipg_mesh* mesh, const double* tau, const double* rhs, double* x, double rtol,
                             int maxit, void* stream, int* iters_out);
+
+/* y = mass_coef M u + A_nu u, the viscous operator of the implicit viscous
+ * step in the paper's divergence form (Sec. 3.2 (iii)): A_nu from
+ * (eps(v), 2 nu eps(u))_e with the symmetric interior-penalty fluxes U* and
+ * F^nu* (penalty tau of Eq. (taue) / Eq. (tau)), homogeneous boundary data;
+ * the three velocity components are coupled.  u, y: DEVICE, 3 * n_dofs doubles
+ * (components x, y, z).  Computed as mass_coef M u + nu L u (the SIPG
+ * Laplacian per component, in the mesh's FP64 arithmetic) plus nu T u, the
+ * transposed-gradient coupling (FP64).  On coarse curved meshes the form may
+ * need a penalty factor above 1 to stay definite (4 wall-normal layers of the
+ * tanh channel at k = 2 need 2). */
+int sipg_apply_viscous_f64(const sipg_mesh* mesh, double mass_coef, double nu, const double* u, double* y,
+                           void* stream);
 
 /* Size in bytes of the static workspace of sipg_cg_solve_noalloc (host output). */
 int sipg_cg_noalloc_capacity(long long* bytes);

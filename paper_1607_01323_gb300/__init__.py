@@ -17,7 +17,8 @@ from . import _lib as L
 __all__ = ["Mesh", "create_mesh", "apply_laplace_f64", "apply_laplace_f32", "apply_helmholtz_f64",
            "apply_helmholtz_f32", "apply_mass_f64", "apply_inverse_mass_f64", "diagonal_f64", "cg_solve",
            "mg_setup", "mg_info", "mg_vcycle", "apply_divergence_f64", "apply_gradient_f64", "tau_div_f64",
-           "apply_divdiv_f64", "project_divdiv_f64", "adjoint_grad_nu", "autotune", "CgResult", "SipgError"]
+           "apply_divdiv_f64", "project_divdiv_f64", "apply_viscous_f64", "adjoint_grad_nu", "autotune", "CgResult",
+           "SipgError"]
 
 SipgError = L.SipgError
 
@@ -319,6 +320,17 @@ def apply_gradient_f64(mesh, p, y=None, stream=None):
         y = torch.empty(3 * mesh.n_dofs, dtype=torch.float64, device=p.device)
     L.check(L.lib().sipg_apply_gradient_f64(mesh.handle, _dev(p, torch.float64, "p"), _vel(mesh, y, "y"),
                                             _stream_ptr(stream)))
+    return y
+
+
+def apply_viscous_f64(mesh, u, mass_coef, nu, y=None, stream=None):
+    """y = mass_coef M u + A_nu u, the divergence-form viscous operator of the
+    implicit viscous step (3 coupled velocity components)."""
+    torch = _torch()
+    if y is None:
+        y = torch.empty_like(u)
+    L.check(L.lib().sipg_apply_viscous_f64(mesh.handle, float(mass_coef), float(nu), _vel(mesh, u, "u"),
+                                           _vel(mesh, y, "y"), _stream_ptr(stream)))
     return y
 
 

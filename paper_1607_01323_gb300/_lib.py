@@ -8,7 +8,7 @@ LIB_PATH = os.path.join(HERE, "libsipg.so")
 OK, MAXITER, EINVAL, ECUDA, ENOMEM, BREAKDOWN, NONFINITE = 0, 1, -1, -2, -3, -4, -5
 BC = {"periodic": 0, "dirichlet": 1, "neumann": 2}
 MAP = {"affine": 0, "channel": 1, "channel_linear": 2}
-OP = {"laplace": 0, "helmholtz": 1}
+OP = {"laplace": 0, "helmholtz": 1, "viscous": 2}
 PC = {"none": 0, "jacobi": 1, "invmass": 2, "cheb_f32": 3, "gmg_f32": 4}
 
 
@@ -60,6 +60,7 @@ _SIGS = {
                               C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "sipg_cg_noalloc_capacity": [C.POINTER(C.c_longlong)],
     "sipg_apply_divergence_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "sipg_apply_viscous_f64": [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_apply_gradient_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_tau_div_f64": [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p],
     "sipg_apply_divdiv_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],

@@ -392,9 +392,18 @@ int sipg_cg_solve(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* 
   if ((st = check_mesh(m))) return st;
   if (!o) return fail(SIPG_EINVAL, "opts is NULL");
   if ((st = check_vec(b, x, ncomp))) return st;
-  if (o->op != SIPG_OP_LAPLACE && o->op != SIPG_OP_HELMHOLTZ) return fail(SIPG_EINVAL, "unknown operator");
+  if (o->op != SIPG_OP_LAPLACE && o->op != SIPG_OP_HELMHOLTZ && o->op != SIPG_OP_VISCOUS)
+    return fail(SIPG_EINVAL, "unknown operator");
   if (o->op == SIPG_OP_HELMHOLTZ && (!(o->mass_coef >= 0.0) || (!o->nu_cell && !(o->nu > 0.0))))
     return fail(SIPG_EINVAL, "Helmholtz needs mass_coef >= 0 and nu > 0");
+  if (o->op == SIPG_OP_VISCOUS) {
+    if (!(o->mass_coef >= 0.0) || !(o->nu > 0.0) || o->nu_cell)
+      return fail(SIPG_EINVAL, "the viscous operator needs mass_coef >= 0, a constant nu > 0 and no nu_cell");
+    if (ncomp != 3) return fail(SIPG_EINVAL, "the viscous operator couples exactly 3 components");
+    if (o->precond != SIPG_PC_NONE && o->precond != SIPG_PC_INVMASS)
+      return fail(SIPG_EINVAL, "the viscous operator supports the preconditioners none and invmass");
+    if (o->zero_mean) return fail(SIPG_EINVAL, "zero_mean applies to the Laplace operator only");
+  }
   if (o->precond < SIPG_PC_NONE || o->precond > SIPG_PC_GMG_F32) return fail(SIPG_EINVAL, "unknown preconditioner");
   if (o->precond == SIPG_PC_GMG_F32) {
     if (o->op != SIPG_OP_LAPLACE) return fail(SIPG_EINVAL, "the multigrid preconditioner supports the Laplace operator");
@@ -508,6 +517,20 @@ int sipg_apply_gradient_f64(const sipg_mesh* m, const double* p, double* y, void
   if (p == y) return fail(SIPG_EINVAL, "p and y must not overlap");
   if ((st = set_device(const_cast<sipg_mesh&>(*m)))) return st;
   return launch_gradient(*m, p, y, (cudaStream_t)stream);
+}
+
+int sipg_apply_viscous_f64(const sipg_mesh* m, double mass_coef, double nu, const double* u, double* y,
+                           void* stream) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!u || !y) return fail(SIPG_EINVAL, "NULL vector");
+  if (u == y) return fail(SIPG_EINVAL, "u and y must not overlap");
+  if (!(mass_coef >= 0.0) || !std::isfinite(mass_coef)) return fail(SIPG_EINVAL, "mass_coef must be finite and >= 0");
+  if (!(nu > 0.0) || !std::isfinite(nu)) return fail(SIPG_EINVAL, "nu must be finite and > 0");
+  if ((st = set_device(*m))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = launch_apply<double>(*m, u, y, 3, mass_coef, nu, nullptr, true, nullptr, nullptr, s))) return st;
+  return launch_viscous_t(*m, u, y, nu, nullptr, s);
 }
 
 int sipg_tau_div_f64(const sipg_mesh* m, const double* u, double zeta, double dt, double* tau, void* stream) {

@@ -407,6 +407,44 @@ __global__ void k_pupdate(const Scalars* __restrict__ sc, long long n, double* _
     p[i] = init ? z[i] : fma(beta, p[i], z[i]);
 }
 
+// x.y of the operator's input and output with the last block forming the
+// total (fixed order) in totals[0] (totals[1], [2] = 0): the p.Ap of an
+// operator applied by several kernels
+__global__ void k_dot_sink(const int* __restrict__ skip, long long n, const double* __restrict__ x,
+                           const double* __restrict__ y, double* __restrict__ part, unsigned* __restrict__ counter,
+                           double* __restrict__ totals) {
+  if (*skip) return;
+  double xy = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    xy += x[i] * y[i];
+  block_partial3(xy, 0.0, 0.0, part);
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+#pragma unroll 4
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(part + 3 * i);
+  double t[3];
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += sh[w];
+    t[0] = tot;
+    totals[0] = t[0];
+    totals[1] = 0.0;
+    totals[2] = 0.0;
+    *counter = 0u;
+  }
+}
+
 // r.r partials only (for separately formed z)
 __global__ void k_dot_rr(const Scalars* __restrict__ sc, long long n, const double* __restrict__ r,
                          double* __restrict__ part) {
@@ -591,7 +629,7 @@ struct Solver {
   long long n;  // total unknowns
   cudaStream_t s;
   Workspace w;
-  bool helm;
+  bool helm, visc;
   double cm, nu;
   const double* nu_cell;
   int nb_apply = 0;
@@ -606,8 +644,9 @@ struct Solver {
   Solver(Mesh& mm, const sipg_cg_opts& oo, int nc, cudaStream_t ss) : m(mm), o(oo), ncomp(nc), s(ss) {
     n = (long long)m.ncell * m.p * m.p * m.p * ncomp;
     helm = o.op == SIPG_OP_HELMHOLTZ;
-    cm = helm ? o.mass_coef : 0.0;
-    nu = helm ? o.nu : 1.0;
+    visc = o.op == SIPG_OP_VISCOUS;
+    cm = (helm || visc) ? o.mass_coef : 0.0;
+    nu = (helm || visc) ? o.nu : 1.0;
     nu_cell = helm ? o.nu_cell : nullptr;
   }
 
@@ -637,7 +676,22 @@ struct Solver {
       // during stream capture only an "external" record becomes a graph node
       cudaEventRecordWithFlags(evs[ev_used].first, s, capturing ? cudaEventRecordExternal : 0);
     }
-    int st = launch_apply<double>(m, x, y, ncomp, cm, nu, nu_cell, true, dots ? &sink : nullptr, nb, s);
+    int st;
+    if (visc) {
+      // divergence-form viscous operator: the SIPG Laplacian of each component,
+      // the transposed-gradient coupling, then the dot products p.Ap
+      DotSink skip_only;
+      skip_only.skip = dots ? &w.sc->done : nullptr;
+      st = launch_apply<double>(m, x, y, ncomp, cm, nu, nullptr, true, &skip_only, nullptr, s);
+      if (!st) st = launch_viscous_t(m, x, y, nu, dots ? &w.sc->done : nullptr, s);
+      if (!st && dots) {
+        k_dot_sink<<<kVecBlocks, kVecThreads, 0, s>>>(&w.sc->done, n, x, y, dots, &w.sc->cnt_apply, w.sc->tot);
+        st = launched();
+        if (nb) *nb = kVecBlocks;
+      }
+    } else {
+      st = launch_apply<double>(m, x, y, ncomp, cm, nu, nu_cell, true, dots ? &sink : nullptr, nb, s);
+    }
     if (m.profile) {
       cudaEventRecordWithFlags(evs[ev_used].second, s, capturing ? cudaEventRecordExternal : 0);
       ++ev_used;

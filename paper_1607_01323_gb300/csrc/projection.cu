@@ -406,6 +406,167 @@ __global__ void divdiv_solve_kernel(Geo<double> g, const double* __restrict__ Cg
   }
 }
 
+// ------------------------------------------------- viscous operator coupling
+// The divergence-form viscous operator of Sec. 3.2 (iii) is nu (L + T) plus
+// the mass term: 2 eps(v):eps(u) = grad v : grad u + grad v : grad u^T and
+// 2 eps(u) n = (grad u) n + (grad u)^T n, so the component-wise SIPG Laplacian
+// L carries the grad u parts and the penalty, and T the transposed-gradient
+// parts:
+//   T(v, u) = sum_e (grad v : grad u^T)_e
+//           - sum_F int ( {{(grad u)^T n}} . [v] + {{(grad v)^T n}} . [u] )
+//           - sum_{F Dirichlet} int ( (grad u)^T n . v + (grad v)^T n . u ).
+// On a face of cell e with outward normal s e_d, ((grad u)^T n)_m = s d_m u_d,
+// so for a test function phi e_i of e the face contributes
+//   (A) -s (phi, {{d_i u_d}})_F      ({{.}}: the own value on a Dirichlet face)
+//   (B) only for i = d: -w s sum_m (d_m phi, J_m)_F with J = u_own - u_nb,
+//       w = 1/2 on an interior face, J = u_own, w = 1 on a Dirichlet face;
+// Neumann faces contribute nothing.  The cell part of output i is
+// sum_j B_(j,i) u_j, B_(j,i) = (d_j phi_a, d_i phi_b): K along i for j = i,
+// else C along j (test derivative) and C^T along i (trial derivative), M along
+// the third direction.  On a d-face, in-face integrals are M / C / C^T along
+// the two tangential directions t1 < t2 (the Jacobians cancel as in C).
+template <int P>
+__global__ void viscous_t_kernel(Geo<double> g, const double* __restrict__ Cg, const double* __restrict__ u,
+                                 double* __restrict__ y, double scale, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  using O = LayerOff<P>;
+  constexpr int P2 = P * P, P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* su = reinterpret_cast<double*>(smraw);  // [3][P3] input
+  double* so = su + 3 * P3;                        // [3][P3] T u
+  double* t1 = so + 3 * P3;
+  double* t2 = t1 + P3;
+  double* C = t2 + P3;
+  double* Ct = C + P2;
+  double* fb = Ct + P2;  // face arrays [11][P2]
+  const int e = blockIdx.x;
+  const long long N = (long long)g.ncell * P3;
+  for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x) su[i] = u[(i / P3) * N + (long long)e * P3 + i % P3];
+  stage_c<P>(Cg, C, Ct);
+  __syncthreads();
+  const CellCtx cc = cell_ctx<P>(g, e, C, Ct);
+  // cell part
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double* A[3] = {cc.L[0] + O::M, cc.L[1] + O::M, cc.L[2] + O::M};
+      if (i == j) {
+        A[i] = cc.L[i] + O::K;
+      } else {
+        A[i] = Ct;
+        A[j] = C;
+      }
+      const double* B[3] = {nullptr, nullptr, nullptr};
+      const double cB[3] = {0.0, 0.0, 0.0};
+      cell_chain<P>(cc, A, B, cB, su + j * P3, so + i * P3, t1, t2, j == 0 ? 0 : 1, 1.0);
+    }
+  // faces
+  const int id[3] = {e % g.n[0], (e / g.n[0]) % g.n[1], e / (g.n[0] * g.n[1])};
+  const bool act = threadIdx.x < P2;
+  const int fb_ = threadIdx.x % P, fc_ = threadIdx.x / P;  // face node along (t1, t2)
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int ta = d == 0 ? 1 : 0;  // t1
+    const int tb = d == 2 ? 1 : 2;  // t2
+    const int sd = d == 0 ? 1 : (d == 1 ? P : P2);
+    const int sa = ta == 0 ? 1 : (ta == 1 ? P : P2);
+    const int sb = tb == 0 ? 1 : (tb == 1 ? P : P2);
+    for (int side = 0; side < 2; ++side) {
+      int nb, kind, jl;
+      face_neighbor(g, d, side, id[d], e, nb, kind, jl);
+      if (kind == SIPG_BC_NEUMANN) continue;  // the same for the whole block
+      const double s = side ? 1.0 : -1.0;
+      const double w = kind == 0 ? 0.5 : 1.0;
+      const int aend = side ? P - 1 : 0;
+      const double* dEnd = cc.L[d] + (side ? O::dR : O::dL);
+      const int base = fb_ * sa + fc_ * sb;  // node (a = 0, b, c)
+      if (act) {
+        double g_own = 0.0;
+#pragma unroll
+        for (int a = 0; a < P; ++a) g_own = fma(dEnd[a], su[d * P3 + base + a * sd], g_own);
+        const double ud = su[d * P3 + base + aend * sd];
+        const double ua = su[ta * P3 + base + aend * sd];
+        const double ub = su[tb * P3 + base + aend * sd];
+        double avgN, avgU, Jd, Ja, Jb;
+        if (kind == 0) {
+          const int nend = P - 1 - aend;
+          const double* dN = g.tab[d] + jl * O::stride + (side ? O::dL : O::dR);
+          const double* un = u + (long long)nb * P3 + base;
+          double g_nb = 0.0;
+#pragma unroll
+          for (int a = 0; a < P; ++a) g_nb = fma(dN[a], un[d * N + a * sd], g_nb);
+          const double udn = un[d * N + nend * sd], uan = un[ta * N + nend * sd], ubn = un[tb * N + nend * sd];
+          avgN = 0.5 * (g_own + g_nb);
+          avgU = 0.5 * (ud + udn);
+          Jd = ud - udn;
+          Ja = ua - uan;
+          Jb = ub - ubn;
+        } else {  // Dirichlet
+          avgN = g_own;
+          avgU = ud;
+          Jd = ud;
+          Ja = ua;
+          Jb = ub;
+        }
+        const int f = fb_ + P * fc_;
+        fb[0 * P2 + f] = avgN;
+        fb[1 * P2 + f] = avgU;
+        fb[2 * P2 + f] = Jd;
+        fb[3 * P2 + f] = Ja;
+        fb[4 * P2 + f] = Jb;
+      }
+      __syncthreads();
+      if (act) {  // contractions along t1 (over b')
+        const double* Ma = cc.L[ta] + O::M;
+        double f1 = 0.0, f2 = 0.0, f3 = 0.0, f4 = 0.0, f5 = 0.0, f6 = 0.0;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int src = q + P * fc_;
+          f1 = fma(Ma[fb_ * P + q], fb[0 * P2 + src], f1);
+          f2 = fma(Ct[fb_ * P + q], fb[1 * P2 + src], f2);
+          f3 = fma(Ma[fb_ * P + q], fb[1 * P2 + src], f3);
+          f4 = fma(Ma[fb_ * P + q], fb[2 * P2 + src], f4);
+          f5 = fma(C[fb_ * P + q], fb[3 * P2 + src], f5);
+          f6 = fma(Ma[fb_ * P + q], fb[4 * P2 + src], f6);
+        }
+        const int f = fb_ + P * fc_;
+        fb[5 * P2 + f] = f1;
+        fb[6 * P2 + f] = f2;
+        fb[7 * P2 + f] = f3;
+        fb[8 * P2 + f] = f4;
+        fb[9 * P2 + f] = f5;
+        fb[10 * P2 + f] = f6;
+      }
+      __syncthreads();
+      if (act) {  // contractions along t2 (over c') and scatter to the own face node / line
+        const double* Mb = cc.L[tb] + O::M;
+        double r1 = 0.0, r5 = 0.0, r6 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0;
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int src = fb_ + P * q;
+          r1 = fma(Mb[fc_ * P + q], fb[5 * P2 + src], r1);
+          r2 = fma(Mb[fc_ * P + q], fb[6 * P2 + src], r2);
+          r3 = fma(Ct[fc_ * P + q], fb[7 * P2 + src], r3);
+          r4 = fma(Mb[fc_ * P + q], fb[8 * P2 + src], r4);
+          r5 = fma(Mb[fc_ * P + q], fb[9 * P2 + src], r5);
+          r6 = fma(C[fc_ * P + q], fb[10 * P2 + src], r6);
+        }
+        const int endn = base + aend * sd;
+        so[d * P3 + endn] += -s * r1 - w * s * (r5 + r6);
+        so[ta * P3 + endn] += -s * r2;
+        so[tb * P3 + endn] += -s * r3;
+        const double rall = -w * s * r4;
+#pragma unroll
+        for (int a = 0; a < P; ++a) so[d * P3 + base + a * sd] = fma(dEnd[a], rall, so[d * P3 + base + a * sd]);
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x) {
+    const long long gi = (i / P3) * N + (long long)e * P3 + i % P3;
+    y[gi] = fma(scale, so[i], y[gi]);
+  }
+}
+
 int cell_threads(int p) { return (p * p + 31) / 32 * 32; }
 
 int proj_cpb(int p) {
@@ -482,6 +643,22 @@ int launch_divdiv_solve_p(const Mesh& m, const double* tau, const double* rhs, d
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "div-div solve launch");
 }
 
+template <int P>
+int launch_viscous_t_p(const Mesh& m, const double* u, double* y, double scale, const int* skip, cudaStream_t s) {
+  constexpr int P3 = P * P * P;
+  const size_t smem = (size_t)(8 * P3 + 2 * P * P + 11 * P * P) * sizeof(double);
+  cudaError_t e;
+  if (smem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(viscous_t_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+          cudaSuccess)
+    return cuda_fail(e, "cudaFuncSetAttribute(viscous coupling)");
+  viscous_t_kernel<P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<double>(m), m.dC64, u, y, scale,
+                                                                       skip);
+  const_cast<Mesh&>(m).launches++;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "viscous coupling launch");
+}
+
 }  // namespace
 
 #define SIPG_PROJ_DISPATCH(CALL)                               \
@@ -516,6 +693,12 @@ int launch_tau_div(const Mesh& m, const double* u, double zeta, double dt, doubl
 
 int launch_divdiv_apply(const Mesh& m, const double* tau, const double* u, double* y, cudaStream_t s) {
 #define CALL(P) launch_divdiv_apply_p<P>(m, tau, u, y, s)
+  SIPG_PROJ_DISPATCH(CALL)
+#undef CALL
+}
+
+int launch_viscous_t(const Mesh& m, const double* u, double* y, double scale, const int* skip, cudaStream_t s) {
+#define CALL(P) launch_viscous_t_p<P>(m, u, y, scale, skip, s)
   SIPG_PROJ_DISPATCH(CALL)
 #undef CALL
 }

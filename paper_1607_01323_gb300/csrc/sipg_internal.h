@@ -179,6 +179,10 @@ int launch_tau_div(const Mesh& m, const double* u, double zeta, double dt, doubl
 int launch_divdiv_apply(const Mesh& m, const double* tau, const double* u, double* y, cudaStream_t s);
 int launch_divdiv_solve(const Mesh& m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
                         int* status_dev, cudaStream_t s);
+// y += scale * T u, the transposed-gradient part of the divergence-form
+// viscous operator (3 components in and out; projection.cu); returns at once
+// when skip is set and *skip != 0
+int launch_viscous_t(const Mesh& m, const double* u, double* y, double scale, const int* skip, cudaStream_t s);
 
 int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s,
                      int* iters, double* relres);
