@@ -39,6 +39,7 @@ Mesh::~Mesh() {
   if (ws) cudaFree(ws);
   if (dC64) cudaFree(dC64);
   if (dC32) cudaFree(dC32);
+  if (dCdf) cudaFree(dCdf);
   for (auto& pr : pending) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);

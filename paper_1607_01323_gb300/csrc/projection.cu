@@ -174,44 +174,45 @@ __global__ void tau_div_kernel(Geo<double> g, const double* __restrict__ u, doub
 
 // ------------------------------------------------------ one-cell operators
 // One thread block per cell; thread t < P^2 owns line t of each phase.
-struct CellCtx {
-  const double* L[3];  // the cell's layer table per direction
-  const double* C;     // C (shared memory)
-  const double* Ct;    // C^T (shared memory)
+template <typename T>
+struct CellCtxT {
+  const T* L[3];  // the cell's layer table per direction
+  const T* C;     // C (shared memory)
+  const T* Ct;    // C^T (shared memory)
   int t;
-  bool active;         // t < P^2
+  bool active;    // t < P^2
 };
+using CellCtx = CellCtxT<double>;
 
 // out (op)= scale * (A_x (x) A_y (x) A_z) in, where direction r's matrix is
 // A_r + c_r B_r (B_r may be null); in, out: [P3]; t1, t2: [P3] scratch.
 // op: 0 store, 1 add.
-template <int P>
-__device__ void cell_chain(const CellCtx& cc, const double* const (&A)[3], const double* const (&B)[3],
-                           const double (&cB)[3], const double* in, double* out, double* t1, double* t2, int op,
-                           double scale) {
+template <int P, typename T>
+__device__ void cell_chain(const CellCtxT<T>& cc, const T* const (&A)[3], const T* const (&B)[3], const T (&cB)[3],
+                           const T* in, T* out, T* t1, T* t2, int op, T scale) {
   const int ti = cc.t % P, tj = cc.t / P;
-  const double* src[3] = {in, t1, t2};
-  double* dst[3] = {t1, t2, out};
+  const T* src[3] = {in, t1, t2};
+  T* dst[3] = {t1, t2, out};
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     if (cc.active) {
       int start, step;
       line_geom<P>(r, ti, tj, start, step);
-      double v[P], w[P];
-      load_line<double, P>(v, src[r], start, step);
+      T v[P], w[P];
+      load_line<T, P>(v, src[r], start, step);
       matvec(w, A[r], v);
       if (B[r]) {
-        double w2[P];
+        T w2[P];
         matvec(w2, B[r], v);
 #pragma unroll
         for (int a = 0; a < P; ++a) w[a] = fma(cB[r], w2[a], w[a]);
       }
       if (r < 2) {
-        store_line<double, P>(dst[r], w, start, step);
+        store_line<T, P>(dst[r], w, start, step);
       } else {
 #pragma unroll
         for (int a = 0; a < P; ++a) {
-          const double val = scale * w[a];
+          const T val = scale * w[a];
           dst[r][start + a * step] = op ? dst[r][start + a * step] + val : val;
         }
       }
@@ -273,10 +274,10 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-template <int P>
-__device__ CellCtx cell_ctx(const Geo<double>& g, int e, const double* C, const double* Ct) {
+template <int P, typename T>
+__device__ CellCtxT<T> cell_ctx(const Geo<T>& g, int e, const T* C, const T* Ct) {
   using O = LayerOff<P>;
-  CellCtx cc;
+  CellCtxT<T> cc;
   const int id[3] = {e % g.n[0], (e / g.n[0]) % g.n[1], e / (g.n[0] * g.n[1])};
   for (int d = 0; d < 3; ++d) cc.L[d] = g.tab[d] + id[d] * O::stride;
   cc.C = C;
@@ -287,8 +288,8 @@ __device__ CellCtx cell_ctx(const Geo<double>& g, int e, const double* C, const 
 }
 
 // stage C and C^T in shared memory
-template <int P>
-__device__ void stage_c(const double* __restrict__ Cg, double* C, double* Ct) {
+template <int P, typename T>
+__device__ void stage_c(const T* __restrict__ Cg, T* C, T* Ct) {
   for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
     const int a = i / P, b = i % P;
     C[i] = Cg[i];
@@ -425,39 +426,40 @@ __global__ void divdiv_solve_kernel(Geo<double> g, const double* __restrict__ Cg
 // else C along j (test derivative) and C^T along i (trial derivative), M along
 // the third direction.  On a d-face, in-face integrals are M / C / C^T along
 // the two tangential directions t1 < t2 (the Jacobians cancel as in C).
-template <int P>
-__global__ void viscous_t_kernel(Geo<double> g, const double* __restrict__ Cg, const double* __restrict__ u,
+template <typename T, int P>
+__global__ void viscous_t_kernel(Geo<T> g, const T* __restrict__ Cg, const double* __restrict__ u,
                                  double* __restrict__ y, double scale, const int* __restrict__ skip) {
   if (skip && *skip) return;
   using O = LayerOff<P>;
   constexpr int P2 = P * P, P3 = P * P * P;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* su = reinterpret_cast<double*>(smraw);  // [3][P3] input
-  double* so = su + 3 * P3;                        // [3][P3] T u
-  double* t1 = so + 3 * P3;
-  double* t2 = t1 + P3;
-  double* C = t2 + P3;
-  double* Ct = C + P2;
-  double* fb = Ct + P2;  // face arrays [11][P2]
+  T* su = reinterpret_cast<T*>(smraw);  // [3][P3] input
+  T* so = su + 3 * P3;                   // [3][P3] T u
+  T* t1 = so + 3 * P3;
+  T* t2 = t1 + P3;
+  T* C = t2 + P3;
+  T* Ct = C + P2;
+  T* fb = Ct + P2;  // face arrays [11][P2]
   const int e = blockIdx.x;
   const long long N = (long long)g.ncell * P3;
-  for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x) su[i] = u[(i / P3) * N + (long long)e * P3 + i % P3];
+  for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x)
+    su[i] = cvt_in<T, double>(u[(i / P3) * N + (long long)e * P3 + i % P3]);
   stage_c<P>(Cg, C, Ct);
   __syncthreads();
-  const CellCtx cc = cell_ctx<P>(g, e, C, Ct);
+  const CellCtxT<T> cc = cell_ctx<P>(g, e, (const T*)C, (const T*)Ct);
   // cell part
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
-      const double* A[3] = {cc.L[0] + O::M, cc.L[1] + O::M, cc.L[2] + O::M};
+      const T* A[3] = {cc.L[0] + O::M, cc.L[1] + O::M, cc.L[2] + O::M};
       if (i == j) {
         A[i] = cc.L[i] + O::K;
       } else {
         A[i] = Ct;
         A[j] = C;
       }
-      const double* B[3] = {nullptr, nullptr, nullptr};
-      const double cB[3] = {0.0, 0.0, 0.0};
-      cell_chain<P>(cc, A, B, cB, su + j * P3, so + i * P3, t1, t2, j == 0 ? 0 : 1, 1.0);
+      const T* B[3] = {nullptr, nullptr, nullptr};
+      const T cB[3] = {T(0), T(0), T(0)};
+      cell_chain<P>(cc, A, B, cB, su + j * P3, so + i * P3, t1, t2, j == 0 ? 0 : 1, T(1));
     }
   // faces
   const int id[3] = {e % g.n[0], (e / g.n[0]) % g.n[1], e / (g.n[0] * g.n[1])};
@@ -474,29 +476,31 @@ __global__ void viscous_t_kernel(Geo<double> g, const double* __restrict__ Cg, c
       int nb, kind, jl;
       face_neighbor(g, d, side, id[d], e, nb, kind, jl);
       if (kind == SIPG_BC_NEUMANN) continue;  // the same for the whole block
-      const double s = side ? 1.0 : -1.0;
-      const double w = kind == 0 ? 0.5 : 1.0;
+      const T s = side ? T(1) : T(-1);
+      const T w = kind == 0 ? T(0.5) : T(1);
       const int aend = side ? P - 1 : 0;
-      const double* dEnd = cc.L[d] + (side ? O::dR : O::dL);
+      const T* dEnd = cc.L[d] + (side ? O::dR : O::dL);
       const int base = fb_ * sa + fc_ * sb;  // node (a = 0, b, c)
       if (act) {
-        double g_own = 0.0;
+        T g_own = T(0);
 #pragma unroll
         for (int a = 0; a < P; ++a) g_own = fma(dEnd[a], su[d * P3 + base + a * sd], g_own);
-        const double ud = su[d * P3 + base + aend * sd];
-        const double ua = su[ta * P3 + base + aend * sd];
-        const double ub = su[tb * P3 + base + aend * sd];
-        double avgN, avgU, Jd, Ja, Jb;
+        const T ud = su[d * P3 + base + aend * sd];
+        const T ua = su[ta * P3 + base + aend * sd];
+        const T ub = su[tb * P3 + base + aend * sd];
+        T avgN, avgU, Jd, Ja, Jb;
         if (kind == 0) {
           const int nend = P - 1 - aend;
-          const double* dN = g.tab[d] + jl * O::stride + (side ? O::dL : O::dR);
+          const T* dN = g.tab[d] + jl * O::stride + (side ? O::dL : O::dR);
           const double* un = u + (long long)nb * P3 + base;
-          double g_nb = 0.0;
+          T g_nb = T(0);
 #pragma unroll
-          for (int a = 0; a < P; ++a) g_nb = fma(dN[a], un[d * N + a * sd], g_nb);
-          const double udn = un[d * N + nend * sd], uan = un[ta * N + nend * sd], ubn = un[tb * N + nend * sd];
-          avgN = 0.5 * (g_own + g_nb);
-          avgU = 0.5 * (ud + udn);
+          for (int a = 0; a < P; ++a) g_nb = fma(dN[a], cvt_in<T, double>(un[d * N + a * sd]), g_nb);
+          const T udn = cvt_in<T, double>(un[d * N + nend * sd]);
+          const T uan = cvt_in<T, double>(un[ta * N + nend * sd]);
+          const T ubn = cvt_in<T, double>(un[tb * N + nend * sd]);
+          avgN = T(0.5) * (g_own + g_nb);
+          avgU = T(0.5) * (ud + udn);
           Jd = ud - udn;
           Ja = ua - uan;
           Jb = ub - ubn;
@@ -516,8 +520,8 @@ __global__ void viscous_t_kernel(Geo<double> g, const double* __restrict__ Cg, c
       }
       __syncthreads();
       if (act) {  // contractions along t1 (over b')
-        const double* Ma = cc.L[ta] + O::M;
-        double f1 = 0.0, f2 = 0.0, f3 = 0.0, f4 = 0.0, f5 = 0.0, f6 = 0.0;
+        const T* Ma = cc.L[ta] + O::M;
+        T f1 = T(0), f2 = T(0), f3 = T(0), f4 = T(0), f5 = T(0), f6 = T(0);
 #pragma unroll
         for (int q = 0; q < P; ++q) {
           const int src = q + P * fc_;
@@ -538,8 +542,8 @@ __global__ void viscous_t_kernel(Geo<double> g, const double* __restrict__ Cg, c
       }
       __syncthreads();
       if (act) {  // contractions along t2 (over c') and scatter to the own face node / line
-        const double* Mb = cc.L[tb] + O::M;
-        double r1 = 0.0, r5 = 0.0, r6 = 0.0, r2 = 0.0, r3 = 0.0, r4 = 0.0;
+        const T* Mb = cc.L[tb] + O::M;
+        T r1 = T(0), r5 = T(0), r6 = T(0), r2 = T(0), r3 = T(0), r4 = T(0);
 #pragma unroll
         for (int q = 0; q < P; ++q) {
           const int src = fb_ + P * q;
@@ -551,19 +555,21 @@ __global__ void viscous_t_kernel(Geo<double> g, const double* __restrict__ Cg, c
           r6 = fma(C[fc_ * P + q], fb[10 * P2 + src], r6);
         }
         const int endn = base + aend * sd;
-        so[d * P3 + endn] += -s * r1 - w * s * (r5 + r6);
-        so[ta * P3 + endn] += -s * r2;
-        so[tb * P3 + endn] += -s * r3;
-        const double rall = -w * s * r4;
+        so[d * P3 + endn] = so[d * P3 + endn] + (-(s * r1) - w * s * (r5 + r6));
+        so[ta * P3 + endn] = so[ta * P3 + endn] + (-(s * r2));
+        so[tb * P3 + endn] = so[tb * P3 + endn] + (-(s * r3));
+        const T rall = -(w * s * r4);
 #pragma unroll
         for (int a = 0; a < P; ++a) so[d * P3 + base + a * sd] = fma(dEnd[a], rall, so[d * P3 + base + a * sd]);
       }
       __syncthreads();
     }
   }
+  // the final accumulation in FP64 (keeps the Laplace part's precision)
+  const T sc = T(scale);
   for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x) {
     const long long gi = (i / P3) * N + (long long)e * P3 + i % P3;
-    y[gi] = fma(scale, so[i], y[gi]);
+    y[gi] = y[gi] + cvt_out<double, T>(sc * so[i]);
   }
 }
 
@@ -648,12 +654,19 @@ int launch_viscous_t_p(const Mesh& m, const double* u, double* y, double scale, 
   constexpr int P3 = P * P * P;
   const size_t smem = (size_t)(8 * P3 + 2 * P * P + 11 * P * P) * sizeof(double);
   cudaError_t e;
-  if (smem > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(viscous_t_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-          cudaSuccess)
-    return cuda_fail(e, "cudaFuncSetAttribute(viscous coupling)");
-  viscous_t_kernel<P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<double>(m), m.dC64, u, y, scale,
-                                                                       skip);
+  if (smem > 48 * 1024) {
+    e = m.f64_arith == SIPG_F64_DOUBLE_FLOAT
+            ? cudaFuncSetAttribute(viscous_t_kernel<dfl, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+            : cudaFuncSetAttribute(viscous_t_kernel<double, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(viscous coupling)");
+  }
+  if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT)
+    viscous_t_kernel<dfl, P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<dfl>(m), m.dCdf, u, y, scale,
+                                                                              skip);
+  else
+    viscous_t_kernel<double, P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<double>(m), m.dC64, u, y,
+                                                                                 scale, skip);
   const_cast<Mesh&>(m).launches++;
   e = cudaGetLastError();
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "viscous coupling launch");

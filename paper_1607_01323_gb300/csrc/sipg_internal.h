@@ -83,6 +83,7 @@ struct Mesh {
   std::vector<double> hC;
   double* dC64 = nullptr;
   float* dC32 = nullptr;
+  dfl* dCdf = nullptr;
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
   int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)

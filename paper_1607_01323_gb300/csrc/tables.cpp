@@ -296,8 +296,12 @@ int build_tables(Mesh& m) {
   {
     if (m.dC64) cudaFree(m.dC64);
     if (m.dC32) cudaFree(m.dC32);
+    if (m.dCdf) cudaFree(m.dCdf);
     m.dC64 = nullptr;
     m.dC32 = nullptr;
+    m.dCdf = nullptr;
+    std::vector<dfl> cd(m.hC.size());
+    for (size_t j = 0; j < cd.size(); ++j) cd[j] = dfl(m.hC[j]);
     std::vector<float> cf(m.hC.begin(), m.hC.end());
     cudaError_t e = cudaMalloc(&m.dC64, m.hC.size() * sizeof(double));
     if (e != cudaSuccess) return fail(SIPG_ENOMEM, "cudaMalloc of the derivative-mass table failed");
@@ -305,6 +309,8 @@ int build_tables(Mesh& m) {
     if (e != cudaSuccess) return fail(SIPG_ENOMEM, "cudaMalloc of the derivative-mass table failed");
     e = cudaMemcpy(m.dC64, m.hC.data(), m.hC.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m.dC32, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&m.dCdf, cd.size() * sizeof(dfl));
+    if (e == cudaSuccess) e = cudaMemcpy(m.dCdf, cd.data(), cd.size() * sizeof(dfl), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload derivative-mass table");
   }
   for (int dir = 0; dir < 3; ++dir) {
