@@ -494,7 +494,8 @@ def run_config(args):
     c1: the 4^3 periodic unit cube at k=3 (operator apply only);
     c3: 3-component viscous Helmholtz on the 64^3 k=3 channel (apply, autotune,
         graph-captured CG with M^-1 and Jacobi), in the Laplace form of the
-        configuration and in the paper's divergence form (coupled components);
+        configuration and in the paper's divergence form (coupled components),
+        and the convective term of the explicit step on the same velocity;
     c4: Neumann-channel Poisson 48^3 k=5, FP32 Chebyshev(4) + FP64 flexible CG
         versus plain FP64 Jacobi CG;
     c5: adjoint gradient on the 32^3 k=3 channel with per-cell viscosity;
@@ -550,6 +551,12 @@ def run_config(args):
                                               precond="invmass", rtol=1e-10), reps=3)
         out["solve_viscous_div_form_invmass_graph"] = {"s": t, "iters": res.iters, "relres": res.relres,
                                                        "dof_applies_per_s": 3 * N * (res.iters + 1) / t}
+        # the convective term of the explicit step (LLF flux, floor(3k/2)+1
+        # Gauss points) on the same mesh and velocity
+        from paper_1607_01323_gb300 import apply_convective_f64
+        t_c, _ = _timed(lambda: apply_convective_f64(m, u, y=y), reps=5)
+        out["apply_convective_llf"] = {"ms": 1e3 * t_c, "dofs": 3 * N, "dofs_per_s": 3 * N / t_c,
+                                       "quadrature_points_per_dir": (3 * 3) // 2 + 1}
     elif args.workload == "c4":
         m = Mesh((48, 48, 48), w["lo"], w["hi"], ("periodic", "neumann", "periodic"),
                  ("periodic", "neumann", "periodic"), mapping="channel", gamma=1.8, k=5)

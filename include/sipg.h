@@ -316,6 +316,20 @@ int sipg_project_divdiv_f64(sipg_mesh* mesh, const double* tau, const double* rh
 int sipg_apply_viscous_f64(const sipg_mesh* mesh, double mass_coef, double nu, const double* u, double* y,
                            void* stream);
 
+/* y = the convective term of the explicit convective step, Eq. (convstepspat):
+ * y_(i,a) = (grad phi_a, u_i u)_e - (phi_a, (F^c* n)_i)_de summed over the
+ * cells, with F^c(u) = u (x) u and the local Lax-Friedrichs flux (Sec. 3.2
+ * (i)): {{u (x) u}} n + Lambda/2 (u^- - u^+) on interior and periodic faces,
+ * Lambda = max(2|u^- . n|, 2|u^+ . n|) per quadrature point; u^- (u^- . n)
+ * + Lambda u^- on no-slip (Dirichlet, g = 0) faces; u^- (u^- . n) on Neumann
+ * faces.  Cell and face integrals use floor(3k/2) + 1 Gauss points per
+ * direction (Sec. 5, over-integration).  u, y: DEVICE, 3 * n_dofs doubles
+ * (components x, y, z), must not overlap; y is overwritten.  Evaluated in the
+ * mesh's FP64 arithmetic (sipg_set_f64_arithmetic).  Nonlinear in u: the
+ * result is not M^-1-scaled (apply sipg_apply_inverse_mass_f64 with ncomp = 3 for
+ * the explicit update). */
+int sipg_apply_convective_f64(const sipg_mesh* mesh, const double* u, double* y, void* stream);
+
 /* Size in bytes of the static workspace of sipg_cg_solve_noalloc (host output). */
 int sipg_cg_noalloc_capacity(long long* bytes);
 

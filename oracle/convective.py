@@ -42,13 +42,14 @@ class ConvectiveOp:
     def _cq(self, e):
         return self.q[self.sipg.cell_key[e]]
 
-    def apply(self, u):
-        """y[i, e, a] = c(phi_a e_i, u) over all cells."""
+    def apply(self, u, cells=None):
+        """y[i, e, a] = c(phi_a e_i, u) for every cell e (or only the cells
+        listed in ``cells``; the other entries stay zero)."""
         spec, P = self.spec, self.P
         u = np.asarray(u, dtype=np.float64).reshape(3, spec.ncell, P)
         y = np.zeros_like(u)
         phi = self.sipg.phi_vol
-        for e in range(spec.ncell):
+        for e in (range(spec.ncell) if cells is None else cells):
             cq = self._cq(e)
             uq = phi @ u[:, e, :].T  # (q, 3)
             F = uq[:, :, None] * uq[:, None, :]  # F[q, i, k] = u_i u_k

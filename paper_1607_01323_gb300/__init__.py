@@ -17,7 +17,7 @@ from . import _lib as L
 __all__ = ["Mesh", "create_mesh", "apply_laplace_f64", "apply_laplace_f32", "apply_helmholtz_f64",
            "apply_helmholtz_f32", "apply_mass_f64", "apply_inverse_mass_f64", "diagonal_f64", "cg_solve",
            "mg_setup", "mg_info", "mg_vcycle", "apply_divergence_f64", "apply_gradient_f64", "tau_div_f64",
-           "apply_divdiv_f64", "project_divdiv_f64", "apply_viscous_f64", "adjoint_grad_nu", "autotune", "CgResult",
+           "apply_divdiv_f64", "project_divdiv_f64", "apply_viscous_f64", "apply_convective_f64", "adjoint_grad_nu", "autotune", "CgResult",
            "SipgError"]
 
 SipgError = L.SipgError
@@ -331,6 +331,17 @@ def apply_viscous_f64(mesh, u, mass_coef, nu, y=None, stream=None):
         y = torch.empty_like(u)
     L.check(L.lib().sipg_apply_viscous_f64(mesh.handle, float(mass_coef), float(nu), _vel(mesh, u, "u"),
                                            _vel(mesh, y, "y"), _stream_ptr(stream)))
+    return y
+
+
+def apply_convective_f64(mesh, u, y=None, stream=None):
+    """y = the convective term of Eq. (convstepspat) with the local
+    Lax-Friedrichs flux and floor(3k/2)+1 Gauss points (3 velocity components)."""
+    torch = _torch()
+    if y is None:
+        y = torch.empty_like(u)
+    L.check(L.lib().sipg_apply_convective_f64(mesh.handle, _vel(mesh, u, "u"), _vel(mesh, y, "y"),
+                                              _stream_ptr(stream)))
     return y
 
 

@@ -62,6 +62,7 @@ _SIGS = {
     "sipg_apply_divergence_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_apply_viscous_f64": [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_apply_gradient_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "sipg_apply_convective_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_tau_div_f64": [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p],
     "sipg_apply_divdiv_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_project_divdiv_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,

@@ -40,6 +40,8 @@ Mesh::~Mesh() {
   if (dC64) cudaFree(dC64);
   if (dC32) cudaFree(dC32);
   if (dCdf) cudaFree(dCdf);
+  if (dconv64) cudaFree(dconv64);
+  if (dconvdf) cudaFree(dconvdf);
   for (auto& pr : pending) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
@@ -532,6 +534,15 @@ int sipg_apply_viscous_f64(const sipg_mesh* m, double mass_coef, double nu, cons
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = launch_apply<double>(*m, u, y, 3, mass_coef, nu, nullptr, true, nullptr, nullptr, s))) return st;
   return launch_viscous_t(*m, u, y, nu, nullptr, s);
+}
+
+int sipg_apply_convective_f64(const sipg_mesh* m, const double* u, double* y, void* stream) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (!u || !y) return fail(SIPG_EINVAL, "NULL vector");
+  if (u == y) return fail(SIPG_EINVAL, "u and y must not overlap");
+  if ((st = set_device(*m))) return st;
+  return launch_convective(*m, u, y, (cudaStream_t)stream);
 }
 
 int sipg_tau_div_f64(const sipg_mesh* m, const double* u, double zeta, double dt, double* tau, void* stream) {

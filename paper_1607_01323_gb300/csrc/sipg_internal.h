@@ -84,6 +84,14 @@ struct Mesh {
   double* dC64 = nullptr;
   float* dC32 = nullptr;
   dfl* dCdf = nullptr;
+  // over-integration tables of the convective term (Sec. 5: floor(3k/2)+1
+  // Gauss points): [Sq: Q x P, l_a(z_q)] [Dq: P x Q, w_q l_a'(z_q)]
+  // [WJ_x: nx x Q] [WJ_y: ny x Q] [WJ_z: nz x Q] with WJ = w_q J(z_q) per layer
+  int nqc = 0;
+  long long conv_off[5] = {0, 0, 0, 0, 0};
+  std::vector<double> hconv;
+  double* dconv64 = nullptr;
+  dfl* dconvdf = nullptr;
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
   int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
@@ -180,6 +188,9 @@ int launch_tau_div(const Mesh& m, const double* u, double zeta, double dt, doubl
 int launch_divdiv_apply(const Mesh& m, const double* tau, const double* u, double* y, cudaStream_t s);
 int launch_divdiv_solve(const Mesh& m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
                         int* status_dev, cudaStream_t s);
+// y = convective term of Eq. (convstepspat) (LLF flux, over-integration;
+// 3 components in and out; convective.cu)
+int launch_convective(const Mesh& m, const double* u, double* y, cudaStream_t s);
 // y += scale * T u, the transposed-gradient part of the divergence-form
 // viscous operator (3 components in and out; projection.cu); returns at once
 // when skip is set and *skip != 0

@@ -292,6 +292,42 @@ int build_tables(Mesh& m) {
       tab[(size_t)i * st + lay_dTR(p)] = tr > ts ? tr - ts : 0.0;
     }
   }
+  // over-integration tables of the convective term
+  {
+    const int Q = (3 * m.k) / 2 + 1;
+    m.nqc = Q;
+    std::vector<double> zo, wo;
+    gauss_rule(Q, zo, wo);
+    std::vector<double> So(Q * p), Dqo(p * Q);
+    for (int q = 0; q < Q; ++q) {
+      std::vector<double> val, der;
+      lagrange_eval(zn, zo[q], val, der);
+      for (int a = 0; a < p; ++a) {
+        So[q * p + a] = val[a];
+        Dqo[a * Q + q] = wo[q] * der[a];
+      }
+    }
+    m.hconv.clear();
+    m.conv_off[0] = 0;
+    m.hconv.insert(m.hconv.end(), So.begin(), So.end());
+    m.conv_off[1] = (long long)m.hconv.size();
+    m.hconv.insert(m.hconv.end(), Dqo.begin(), Dqo.end());
+    for (int dir = 0; dir < 3; ++dir) {
+      m.conv_off[2 + dir] = (long long)m.hconv.size();
+      const int n = m.desc.n[dir];
+      for (int i = 0; i < n; ++i) {
+        std::vector<long double> X(p);
+        for (int a = 0; a < p; ++a) X[a] = map_coord(m.desc, dir, (i + zn[a]) / n);
+        for (int q = 0; q < Q; ++q) {
+          std::vector<double> val, der;
+          lagrange_eval(zn, zo[q], val, der);
+          long double J = 0.0L;
+          for (int a = 0; a < p; ++a) J += X[a] * der[a];
+          m.hconv.push_back((double)(wo[q] * J));
+        }
+      }
+    }
+  }
   // upload (double, float and double-float copies)
   {
     if (m.dC64) cudaFree(m.dC64);
@@ -311,6 +347,17 @@ int build_tables(Mesh& m) {
     if (e == cudaSuccess) e = cudaMemcpy(m.dC32, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&m.dCdf, cd.size() * sizeof(dfl));
     if (e == cudaSuccess) e = cudaMemcpy(m.dCdf, cd.data(), cd.size() * sizeof(dfl), cudaMemcpyHostToDevice);
+    if (m.dconv64) cudaFree(m.dconv64);
+    if (m.dconvdf) cudaFree(m.dconvdf);
+    m.dconv64 = nullptr;
+    m.dconvdf = nullptr;
+    std::vector<dfl> cvd(m.hconv.size());
+    for (size_t j = 0; j < cvd.size(); ++j) cvd[j] = dfl(m.hconv[j]);
+    if (e == cudaSuccess) e = cudaMalloc(&m.dconv64, m.hconv.size() * sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(m.dconv64, m.hconv.data(), m.hconv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&m.dconvdf, cvd.size() * sizeof(dfl));
+    if (e == cudaSuccess) e = cudaMemcpy(m.dconvdf, cvd.data(), cvd.size() * sizeof(dfl), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload derivative-mass table");
   }
   for (int dir = 0; dir < 3; ++dir) {
