@@ -554,8 +554,12 @@ def run_config(args):
         # the convective term of the explicit step (LLF flux, floor(3k/2)+1
         # Gauss points) on the same mesh and velocity
         from paper_1607_01323_gb300 import apply_convective_f64
+        cpb_c = m.cells_per_block(2)
+        t_c0, _ = _timed(lambda: apply_convective_f64(m, u, y=y), reps=5)
+        cpb_ct = autotune(m, 2)
         t_c, _ = _timed(lambda: apply_convective_f64(m, u, y=y), reps=5)
-        out["apply_convective_llf"] = {"ms": 1e3 * t_c, "dofs": 3 * N, "dofs_per_s": 3 * N / t_c,
+        out["apply_convective_llf"] = {"ms_default_cpb": 1e3 * t_c0, "cpb_default": cpb_c, "cpb_autotuned": cpb_ct,
+                                       "ms": 1e3 * t_c, "dofs": 3 * N, "dofs_per_s": 3 * N / t_c,
                                        "quadrature_points_per_dir": (3 * 3) // 2 + 1}
     elif args.workload == "c4":
         m = Mesh((48, 48, 48), w["lo"], w["hi"], ("periodic", "neumann", "periodic"),

@@ -345,7 +345,8 @@ int sipg_adjoint_grad_nu(const sipg_mesh* mesh, const double* nu_cell, const dou
 /* Choose the cells-per-block of the operator kernels for this mesh and
  * precision (0 = FP64, 1 = FP32) by timing the candidates with CUDA events.
  * If cache_path is not NULL the choice is read from / appended to that text
- * file (one "key value" line per (k, precision, map, mesh size)). */
+ * file (one "key value" line per (k, precision, map, mesh size)).  precision
+ * 2 tunes the convective kernel for the mesh's current FP64 arithmetic. */
 int sipg_autotune(sipg_mesh* mesh, int precision, const char* cache_path);
 
 /* Arithmetic of the FP64 operator entry points (sipg_apply_laplace_f64,
@@ -371,7 +372,9 @@ int sipg_get_f64_arithmetic(const sipg_mesh* mesh, int* mode);
 typedef enum { SIPG_THREADS_LINE = 0, SIPG_THREADS_PLANE = 1 } sipg_threads;
 int sipg_set_f32_mapping(sipg_mesh* mesh, int mapping);
 
-/* Cells per block currently used for a precision (host output). */
+/* Cells per block currently used for a precision (host output).  precision
+ * 2 addresses the kernel of sipg_apply_convective_f64 (cells of one thread
+ * block; 0 < cpb <= the count whose shared memory fits 200 KB). */
 int sipg_get_cells_per_block(const sipg_mesh* mesh, int precision, int* cpb);
 int sipg_set_cells_per_block(sipg_mesh* mesh, int precision, int cpb);
 

@@ -634,8 +634,8 @@ int sipg_get_f64_arithmetic(const sipg_mesh* m, int* mode) {
 int sipg_get_cells_per_block(const sipg_mesh* m, int precision, int* cpb) {
   int st;
   if ((st = check_mesh(m))) return st;
-  if (!cpb || (precision != 0 && precision != 1)) return fail(SIPG_EINVAL, "bad argument");
-  *cpb = cells_per_block(*m, precision);
+  if (!cpb || precision < 0 || precision > 2) return fail(SIPG_EINVAL, "bad argument");
+  *cpb = precision == 2 ? convective_cpb(*m, nullptr) : cells_per_block(*m, precision);
   return SIPG_OK;
 }
 
@@ -651,7 +651,14 @@ int sipg_set_f32_mapping(sipg_mesh* m, int mapping) {
 int sipg_set_cells_per_block(sipg_mesh* m, int precision, int cpb) {
   int st;
   if ((st = check_mesh(m))) return st;
-  if (precision != 0 && precision != 1) return fail(SIPG_EINVAL, "precision must be 0 or 1");
+  if (precision == 2) {
+    int mx = 1;
+    convective_cpb(*m, &mx);
+    if (cpb < 1 || cpb > mx) return fail(SIPG_EINVAL, "cells per block out of range for this degree");
+    m->cpb_conv = cpb;
+    return SIPG_OK;
+  }
+  if (precision != 0 && precision != 1) return fail(SIPG_EINVAL, "precision must be 0, 1 or 2");
   const size_t elt = precision == 0 ? 8 : 4;
   if (cpb < 1 || (cpb * m->p * m->p + 31) / 32 * 32 > kMaxCellThreads || (size_t)3 * cpb * m->p * m->p * m->p * elt > 200 * 1024)
     return fail(SIPG_EINVAL, "cells per block out of range for this degree");
@@ -659,13 +666,66 @@ int sipg_set_cells_per_block(sipg_mesh* m, int precision, int cpb) {
   return SIPG_OK;
 }
 
+// Cells per block of the convective kernel: every feasible count, timed on a
+// zero velocity field (the kernel's work does not depend on the values).
+static int autotune_convective(sipg_mesh* m, int* best_out) {
+  int st;
+  if ((st = set_device(*m))) return st;
+  int mx = 1;
+  convective_cpb(*m, &mx);
+  const long long n = 3 * n_dofs(*m);
+  double *x = nullptr, *y = nullptr;
+  cudaError_t e = cudaMalloc(&x, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&y, n * sizeof(double));
+  if (e != cudaSuccess) {
+    if (x) cudaFree(x);
+    return fail(SIPG_ENOMEM, "autotune buffers");
+  }
+  cudaMemset(x, 0, n * sizeof(double));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int old = m->cpb_conv;
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int c = 1; c <= mx; ++c) {
+    m->cpb_conv = c;
+    float tot = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      cudaEventRecord(e0, 0);
+      for (int it = 0; it < 2; ++it)
+        if (launch_convective(*m, x, y, 0)) ok = false;
+      cudaEventRecord(e1, 0);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tot += ms;  // first repetition is warm-up
+    }
+    if (ok && tot < best_ms) {
+      best_ms = tot;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(x);
+  cudaFree(y);
+  cudaGetLastError();
+  m->cpb_conv = best ? best : old;
+  if (!best) return fail(SIPG_ECUDA, "autotune: no candidate ran");
+  *best_out = best;
+  return SIPG_OK;
+}
+
 int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
   int st;
   if ((st = check_mesh(m))) return st;
-  if (precision != 0 && precision != 1) return fail(SIPG_EINVAL, "precision must be 0 or 1");
+  if (precision < 0 || precision > 2) return fail(SIPG_EINVAL, "precision must be 0, 1 or 2");
   char key[160];
-  std::snprintf(key, sizeof(key), "k=%d prec=%d map=%d n=%dx%dx%d", m->k, precision, m->desc.map, m->desc.n[0],
-                m->desc.n[1], m->desc.n[2]);
+  std::snprintf(key, sizeof(key), "k=%d prec=%d map=%d n=%dx%dx%d%s", m->k, precision, m->desc.map, m->desc.n[0],
+                m->desc.n[1], m->desc.n[2],
+                precision == 2 ? (m->f64_arith == SIPG_F64_DOUBLE_FLOAT ? " arith=df" : " arith=native") : "");
   if (cache_path) {
     std::ifstream f(cache_path);
     std::string line;
@@ -676,6 +736,15 @@ int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
         if (sipg_set_cells_per_block(m, precision, c) == SIPG_OK) return SIPG_OK;
       }
     }
+  }
+  if (precision == 2) {
+    int best = 0;
+    if ((st = autotune_convective(m, &best))) return st;
+    if (cache_path) {
+      std::ofstream f(cache_path, std::ios::app);
+      if (f) f << key << " cpb=" << best << "\n";
+    }
+    return SIPG_OK;
   }
   if ((st = set_device(*m))) return st;
   const size_t elt = precision == 0 ? 8 : 4;

@@ -95,6 +95,7 @@ struct Mesh {
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
   int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
+  int cpb_conv = 0;     // cells per block of the convective kernel (0 = default)
   // profiling
   bool profile = false;
   double prof_ms = 0.0;
@@ -191,6 +192,8 @@ int launch_divdiv_solve(const Mesh& m, const double* tau, const double* rhs, dou
 // y = convective term of Eq. (convstepspat) (LLF flux, over-integration;
 // 3 components in and out; convective.cu)
 int launch_convective(const Mesh& m, const double* u, double* y, cudaStream_t s);
+// cells per block the convective kernel uses; *max_cpb = the largest that fits
+int convective_cpb(const Mesh& m, int* max_cpb);
 // y += scale * T u, the transposed-gradient part of the divergence-form
 // viscous operator (3 components in and out; projection.cu); returns at once
 // when skip is set and *skip != 0

@@ -120,3 +120,23 @@ def test_convective_errors():
     with pytest.raises(ValueError):
         apply_convective_f64(m, u[: m.n_dofs])
     assert torch.isfinite(apply_convective_f64(m, u)).all()
+
+
+def test_convective_cells_per_block():
+    """Every feasible cells-per-block gives the same bits (the cells of a block
+    do not interact), including a ragged last block."""
+    from paper_1607_01323_gb300 import SipgError, apply_convective_f64
+    c = channel((3, 5, 3))
+    m = gpu_mesh(c, 3)
+    u = _cuda(uniform(3 * m.n_dofs, "u", seed=7))
+    ref = apply_convective_f64(m, u)
+    cpb = 1
+    while True:
+        try:
+            m.set_cells_per_block(2, cpb)
+        except SipgError:
+            break
+        assert m.cells_per_block(2) == cpb
+        assert torch.equal(apply_convective_f64(m, u), ref), cpb
+        cpb += 1
+    assert cpb > 2
