@@ -452,6 +452,34 @@ def run_apply_only(args):
         print("apply %s n=%s k=%d dofs=%d: %.4f ms" % (args.precision, n, k, m.n_dofs, ev[0].elapsed_time(ev[1])))
 
 
+def run_convective_only(args):
+    """A few convective-term applies on the bench channel (or --cells/--k)
+    with a laminar profile plus noise, timed with CUDA events; for ncu captures."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1607_01323_gb300 import Mesh, apply_convective_f64, inputs
+    w = dict(WORKLOAD)
+    n = (args.cells,) * 3 if args.cells else w["n"]
+    k = args.k if args.k else w["k"]
+    m = Mesh(n, w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"], k=k)
+    m.set_f64_arithmetic(args.f64)
+    N = m.n_dofs
+    X = m.node_coordinates()
+    u = torch.tensor(np.concatenate([(1 - X[:, 1] ** 2) + 0.1 * inputs.normal(0, "ux", N),
+                                     0.1 * inputs.normal(0, "uy", N), 0.1 * inputs.normal(0, "uz", N)]),
+                     device="cuda")
+    y = torch.empty_like(u)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for i in range(args.reps):
+        ev[0].record()
+        apply_convective_f64(m, u, y=y)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print("convective %s n=%s k=%d dofs=%d: %.4f ms" % (args.f64, n, k, 3 * N, ev[0].elapsed_time(ev[1])))
+
+
 def run_vcycle_only(args):
     """Multigrid set-up and a few V-cycles on the bench mesh (or --cells/--k),
     timed with CUDA events; for ncu launch lists of the V-cycle."""
@@ -652,8 +680,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "vcycle"],
-                    help="apply: only operator applies; vcycle: only multigrid V-cycles")
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "vcycle", "convective"],
+                    help="apply: only operator applies; vcycle: only multigrid V-cycles; convective: only "
+                         "convective-term applies")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--cells", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
@@ -667,6 +696,8 @@ def main():
         run_apply_only(args)
     elif args.mode == "vcycle":
         run_vcycle_only(args)
+    elif args.mode == "convective":
+        run_convective_only(args)
     elif args.workload != "c2":
         run_config(args)
     elif args.impl == "reference":
