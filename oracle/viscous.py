@@ -105,15 +105,15 @@ class ViscousOp:
             cq = self._cq(e)
             g = cq.grad
             # cell: nu (grad v : grad u + grad v : grad u^T) and the mass
-            lap = np.einsum("q,qak,qbk->ab", cq.wdet, g, g)
+            lap = np.einsum("q,qak,qbk->ab", cq.wdet, g, g, optimize=True)
             B = np.zeros((3, P, 3, P))
             for i in range(3):
                 B[i, :, i, :] += nu * lap
                 for j in range(3):
-                    B[i, :, j, :] += nu * np.einsum("q,qa,qb->ab", cq.wdet, g[:, :, j], g[:, :, i])
+                    B[i, :, j, :] += nu * np.einsum("q,qa,qb->ab", cq.wdet, g[:, :, j], g[:, :, i], optimize=True)
             if mass_coef:
                 phi = self.sipg.phi_vol
-                Mloc = np.einsum("q,qa,qb->ab", cq.wdet, phi, phi)
+                Mloc = np.einsum("q,qa,qb->ab", cq.wdet, phi, phi, optimize=True)
                 for i in range(3):
                     B[i, :, i, :] += mass_coef * Mloc
             add(self._gidx(e), self._gidx(e), B.reshape(3 * P, 3 * P))
@@ -134,16 +134,16 @@ class ViscousOp:
                         for t in (0, 1):
                             for s in (0, 1):
                                 # - {{2 eps(u)}} n . [v] - {{2 eps(v)}} n . [u] + tau [u].[v]
-                                Bf = -0.5 * sig[t] * np.einsum("q,qam,qbm->ab", wA, Vs[t], Ts[s])
-                                Bf += -0.5 * sig[s] * np.einsum("q,qam,qbm->ab", wA, Ts[t], Vs[s])
+                                Bf = -0.5 * sig[t] * np.einsum("q,qam,qbm->ab", wA, Vs[t], Ts[s], optimize=True)
+                                Bf += -0.5 * sig[s] * np.einsum("q,qam,qbm->ab", wA, Ts[t], Vs[s], optimize=True)
                                 Bf *= nu
-                                Bf += tauF * nu * sig[t] * sig[s] * np.einsum("q,qam,qbm->ab", wA, Vs[t], Vs[s])
+                                Bf += tauF * nu * sig[t] * sig[s] * np.einsum("q,qam,qbm->ab", wA, Vs[t], Vs[s], optimize=True)
                                 add(idx[t], idx[s], Bf)
                     elif self.sipg.bkind[(d, side)] == DIRICHLET:
                         V = _values(phif)
                         T = _traction(gradf, n)
-                        Bf = -nu * (np.einsum("q,qam,qbm->ab", wA, V, T) + np.einsum("q,qam,qbm->ab", wA, T, V))
-                        Bf += 2.0 * tau[e] * nu * np.einsum("q,qam,qbm->ab", wA, V, V)
+                        Bf = -nu * (np.einsum("q,qam,qbm->ab", wA, V, T, optimize=True) + np.einsum("q,qam,qbm->ab", wA, T, V, optimize=True))
+                        Bf += 2.0 * tau[e] * nu * np.einsum("q,qam,qbm->ab", wA, V, V, optimize=True)
                         add(self._gidx(e), self._gidx(e), Bf)
                     elif self.sipg.bkind[(d, side)] not in (NEUMANN, PERIODIC):
                         raise ValueError("unknown boundary condition")
