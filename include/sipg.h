@@ -330,6 +330,91 @@ int sipg_apply_viscous_f64(const sipg_mesh* mesh, double mass_coef, double nu, c
  * the explicit update). */
 int sipg_apply_convective_f64(const sipg_mesh* mesh, const double* u, double* y, void* stream);
 
+/* ------------------------------------------------------------------------
+ * The dual-splitting time step (Sec. 2.2) with the spatial variant V3c.
+ *
+ * One step from t^n to t^(n+1) = t^n + dt with the order-J BDF / extrapolation
+ * pair (gamma0, alpha_i, beta_i of Karniadakis, Israeli and Orszag 1991):
+ *  (i)   M u_hat = (M sum alpha_i u^(n-i) + dt sum beta_i C(u^(n-i)) + dt M f) / gamma0,
+ *        C the convective term of sipg_apply_convective_f64, f a constant body
+ *        force (Eq. (convstepspat));
+ *  (ii)  L_N p = (gamma0/dt) D u_hat + (q, h)_walls with D of Eq. (av3), L_N the
+ *        SIPG Laplacian with Neumann data on the no-slip walls, and
+ *        h = -(sum beta_i (div F^c(u^(n-i)) + nu curl omega^(n-i)) - f) . n, the
+ *        flux Pi* of Eq. (ipflux) (omega the cell-wise L2 projection of curl u,
+ *        evaluated from the wall cell at the k+1 Gauss points of each wall
+ *        face); solved for the zero-mean p by CG (Jacobi or the FP32 multigrid
+ *        V-cycle);
+ *  (iii) (M + tau_D B) u_hathat = M u_hat + (dt/gamma0) G p, Eq. (div-div) with G
+ *        of Eq. (bv3) and tau_D of Eq. (tauD) from u^n (per-cell CG);
+ *  (iv)  ((gamma0/dt) M + A_nu) u^(n+1) = (gamma0/dt) M u_hathat with the
+ *        divergence-form viscous operator (M^-1-preconditioned CG).
+ * Velocity boundaries: periodic sides and no-slip walls (SIPG_BC_DIRICHLET,
+ * g_u = 0); SIPG_BC_NEUMANN (outflow) sides are rejected.  Until `order`
+ * levels are known the order rises one step at a time. */
+typedef struct sipg_ns sipg_ns; /* opaque, owned by the library */
+
+typedef struct {
+  int k;                    /* polynomial degree, 2..7 (the pressure data need k >= 2)   */
+  double penalty;           /* penalty factor of the SIPG forms (>= 1 recommended)     */
+  double nu;                /* kinematic viscosity, > 0                                 */
+  double dt;                /* time step, > 0                                           */
+  int order;                /* J = 1, 2 or 3                                            */
+  double zeta;              /* div-div factor zeta_D >= 0 of Eq. (tauD); 0 = no penalty  */
+  int pressure_precond;     /* SIPG_PC_JACOBI or SIPG_PC_GMG_F32                         */
+  double rtol_pressure;     /* CG stopping tolerances (relative residual)              */
+  double rtol_viscous;
+  double rtol_projection;   /* per-cell tolerance of the local projection              */
+  int maxit;                /* iteration bound of the pressure and viscous CG          */
+  int maxit_projection;     /* iteration bound of each cell's projection CG            */
+} sipg_ns_params;
+
+typedef struct {
+  int order;                /* BDF order used in this step                          */
+  int pressure_iters, viscous_iters, projection_iters;
+  double pressure_relres, viscous_relres;
+} sipg_ns_stats;
+
+/* Defaults: k = 3, penalty 1, nu = 1/180, dt = 1e-3, order 3, zeta 1, Jacobi,
+ * tolerances 1e-10 (pressure, viscous) and 1e-10 (projection), maxit 10000,
+ * projection maxit 500. */
+int sipg_ns_default_params(sipg_ns_params* prm);
+
+/* Create a stepper on the current device for the velocity boundaries of desc
+ * (the pressure mesh swaps no-slip walls for Neumann sides).  Allocates
+ * about 18 velocity-sized vectors.  Errors: EINVAL, ENOMEM, ECUDA. */
+int sipg_ns_create(const sipg_mesh_desc* desc, const sipg_ns_params* prm, sipg_ns** out);
+int sipg_ns_destroy(sipg_ns* ns);
+
+/* The stepper's meshes (owned by the stepper): which = 0 velocity (walls
+ * Dirichlet), 1 pressure (walls Neumann).  Same geometry and node order. */
+int sipg_ns_mesh(sipg_ns* ns, int which, sipg_mesh** out);
+
+/* Set time level n - level (level 0 = the current velocity; level 0 resets the
+ * history to one level, level i > 0 then adds older levels in order).
+ * u: DEVICE, 3 * n_dofs doubles (components x, y, z), copied.  Computes the
+ * level's convective term and wall data.  Synchronous. */
+int sipg_ns_set_velocity(sipg_ns* ns, int level, const double* u, void* stream);
+
+/* Advance one step with the body force f (HOST, 3 doubles, or NULL = 0) at
+ * t^(n+1).  Synchronous (the solves read convergence data).  stats (HOST) may
+ * be NULL.  Returns SIPG_MAXITER if a solve stopped at its bound, the
+ * solvers' statuses otherwise. */
+int sipg_ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stats);
+
+/* Copy the current velocity (3 * n_dofs) or pressure (n_dofs) to DEVICE
+ * memory of the caller.  The pressure is determined up to an additive
+ * constant (Neumann walls and periodic sides): the zero-mean CG fixes its
+ * residual, not its mean. */
+int sipg_ns_velocity(const sipg_ns* ns, double* u, void* stream);
+int sipg_ns_pressure(const sipg_ns* ns, double* p, void* stream);
+
+/* The wall data (div F^c(u) + nu curl omega) . n of the current velocity at
+ * the (k+1)^2 Gauss points of every wall face (DEVICE, *count doubles; faces
+ * ordered by cell, then direction, then low/high side; points with the first
+ * tangential direction fastest).  h may be NULL to query *count (HOST). */
+int sipg_ns_wall_data(const sipg_ns* ns, double* h, long long* count, void* stream);
+
 /* Size in bytes of the static workspace of sipg_cg_solve_noalloc (host output). */
 int sipg_cg_noalloc_capacity(long long* bytes);
 

@@ -17,7 +17,7 @@ from . import _lib as L
 __all__ = ["Mesh", "create_mesh", "apply_laplace_f64", "apply_laplace_f32", "apply_helmholtz_f64",
            "apply_helmholtz_f32", "apply_mass_f64", "apply_inverse_mass_f64", "diagonal_f64", "cg_solve",
            "mg_setup", "mg_info", "mg_vcycle", "apply_divergence_f64", "apply_gradient_f64", "tau_div_f64",
-           "apply_divdiv_f64", "project_divdiv_f64", "apply_viscous_f64", "apply_convective_f64", "adjoint_grad_nu", "autotune", "CgResult",
+           "apply_divdiv_f64", "project_divdiv_f64", "apply_viscous_f64", "apply_convective_f64", "NavierStokes", "adjoint_grad_nu", "autotune", "CgResult",
            "SipgError"]
 
 SipgError = L.SipgError
@@ -75,8 +75,19 @@ class Mesh:
         self.set_degree(k)
         self.set_penalty(penalty)
 
+    @classmethod
+    def _view(cls, handle, owner, n, bc_lo, bc_hi, mapping, gamma, k, penalty):
+        """A mesh owned by another library object (kept alive through `owner`)."""
+        m = cls.__new__(cls)
+        m._h, m._owner = handle, owner
+        m.n, m.bc_lo, m.bc_hi = tuple(n), tuple(bc_lo), tuple(bc_hi)
+        m.mapping, m.gamma, m.k, m.p, m.penalty = mapping, gamma, int(k), int(k) + 1, float(penalty)
+        return m
+
     def __del__(self):
         h = getattr(self, "_h", None)
+        if getattr(self, "_owner", None) is not None:
+            return
         if h is not None and h.value and L._lib is not None:
             L._lib.sipg_destroy_mesh(h)
             self._h = None
@@ -391,3 +402,86 @@ def adjoint_grad_nu(mesh, nu_cell, u, lam, out=None, stream=None):
 def autotune(mesh, precision=0, cache_path=None):
     L.check(L.lib().sipg_autotune(mesh.handle, int(precision), cache_path.encode() if cache_path else None))
     return mesh.cells_per_block(precision)
+
+
+class NavierStokes:
+    """The dual-splitting time step (Sec. 2.2, variant V3c) on the device:
+    explicit convective step, pressure Poisson equation with the wall data of
+    Eq. (ipflux), div-div penalised projection, implicit viscous step, BDF
+    order 1-3.  Velocity boundaries: periodic or no-slip walls ("dirichlet")."""
+
+    def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc_lo=("periodic",) * 3,
+                 bc_hi=("periodic",) * 3, mapping="affine", gamma=1.8, k=3, nu=1.0 / 180.0, dt=1e-3, order=3,
+                 zeta=1.0, pressure_precond="jacobi", rtol_pressure=1e-10, rtol_viscous=1e-10,
+                 rtol_projection=1e-10, maxit=10000, maxit_projection=500, penalty=1.0, f64_arithmetic=None):
+        lib = L.lib()
+        d = L.MeshDesc()
+        for i in range(3):
+            d.n[i], d.lo[i], d.hi[i] = int(n[i]), float(lo[i]), float(hi[i])
+            d.bc_lo[i], d.bc_hi[i] = L.BC[bc_lo[i]], L.BC[bc_hi[i]]
+        d.map, d.gamma = L.MAP[mapping], float(gamma)
+        prm = L.NsParams()
+        L.check(lib.sipg_ns_default_params(C.byref(prm)))
+        prm.k, prm.penalty, prm.nu, prm.dt, prm.order, prm.zeta = int(k), float(penalty), float(nu), float(dt), \
+            int(order), float(zeta)
+        prm.pressure_precond = L.PC[pressure_precond]
+        prm.rtol_pressure, prm.rtol_viscous, prm.rtol_projection = rtol_pressure, rtol_viscous, rtol_projection
+        prm.maxit, prm.maxit_projection = int(maxit), int(maxit_projection)
+        h = C.c_void_p()
+        L.check(lib.sipg_ns_create(C.byref(d), C.byref(prm), C.byref(h)))
+        self._h = h
+        self.params = prm
+        pbc = lambda bcs: tuple("neumann" if b == "dirichlet" else b for b in bcs)
+        meshes = []
+        for which, (bl, bh) in enumerate(((bc_lo, bc_hi), (pbc(bc_lo), pbc(bc_hi)))):
+            mh = C.c_void_p()
+            L.check(lib.sipg_ns_mesh(h, which, C.byref(mh)))
+            meshes.append(Mesh._view(mh, self, n, bl, bh, mapping, gamma, k, penalty))
+        self.velocity_mesh, self.pressure_mesh = meshes
+        if f64_arithmetic is not None:
+            for m in meshes:
+                m.set_f64_arithmetic(f64_arithmetic)
+        self.n_dofs = self.velocity_mesh.n_dofs
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and L._lib is not None:
+            L._lib.sipg_ns_destroy(h)
+            self._h = None
+
+    def set_velocity(self, u, level=0, stream=None):
+        """Time level n - level (0: current; then 1, 2 in order); u: 3 * n_dofs on the device."""
+        L.check(L.lib().sipg_ns_set_velocity(self._h, int(level), _vel(self.velocity_mesh, u, "u"),
+                                             _stream_ptr(stream)))
+
+    def step(self, f=(0.0, 0.0, 0.0), stream=None):
+        """One step with the constant body force f; returns the solver statistics."""
+        fa = (C.c_double * 3)(*[float(v) for v in f])
+        st = L.NsStats()
+        L.check(L.lib().sipg_ns_step(self._h, fa, _stream_ptr(stream), C.byref(st)))
+        return {k: getattr(st, k) for k, _ in L.NsStats._fields_}
+
+    def velocity(self, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(3 * self.n_dofs, dtype=torch.float64, device="cuda")
+        L.check(L.lib().sipg_ns_velocity(self._h, _vel(self.velocity_mesh, out, "out"), _stream_ptr(stream)))
+        return out
+
+    def pressure(self, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.n_dofs, dtype=torch.float64, device="cuda")
+        L.check(L.lib().sipg_ns_pressure(self._h, _dev(out, torch.float64, "out"), _stream_ptr(stream)))
+        return out
+
+    def wall_data(self, stream=None):
+        """(div F^c(u) + nu curl omega) . n of the current velocity at the Gauss
+        points of the wall faces (faces by cell, direction, side)."""
+        torch = _torch()
+        cnt = C.c_longlong()
+        L.check(L.lib().sipg_ns_wall_data(self._h, None, C.byref(cnt), None))
+        out = torch.empty(max(cnt.value, 1), dtype=torch.float64, device="cuda")
+        L.check(L.lib().sipg_ns_wall_data(self._h, _dev(out, torch.float64, "out"), C.byref(cnt),
+                                          _stream_ptr(stream)))
+        return out[: cnt.value]

@@ -26,6 +26,18 @@ class CgOpts(C.Structure):
                 ("mg_coarse_tol", C.c_double), ("mg_coarse_maxdeg", C.c_int)]
 
 
+class NsParams(C.Structure):
+    _fields_ = [("k", C.c_int), ("penalty", C.c_double), ("nu", C.c_double), ("dt", C.c_double),
+                ("order", C.c_int), ("zeta", C.c_double), ("pressure_precond", C.c_int),
+                ("rtol_pressure", C.c_double), ("rtol_viscous", C.c_double), ("rtol_projection", C.c_double),
+                ("maxit", C.c_int), ("maxit_projection", C.c_int)]
+
+
+class NsStats(C.Structure):
+    _fields_ = [("order", C.c_int), ("pressure_iters", C.c_int), ("viscous_iters", C.c_int),
+                ("projection_iters", C.c_int), ("pressure_relres", C.c_double), ("viscous_relres", C.c_double)]
+
+
 class SipgError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("libsipg status %d: %s" % (status, msg))
@@ -63,6 +75,15 @@ _SIGS = {
     "sipg_apply_viscous_f64": [C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_apply_gradient_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_apply_convective_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "sipg_ns_default_params": [C.POINTER(NsParams)],
+    "sipg_ns_create": [C.POINTER(MeshDesc), C.POINTER(NsParams), C.POINTER(C.c_void_p)],
+    "sipg_ns_destroy": [C.c_void_p],
+    "sipg_ns_mesh": [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)],
+    "sipg_ns_set_velocity": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
+    "sipg_ns_step": [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(NsStats)],
+    "sipg_ns_velocity": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "sipg_ns_pressure": [C.c_void_p, C.c_void_p, C.c_void_p],
+    "sipg_ns_wall_data": [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong), C.c_void_p],
     "sipg_tau_div_f64": [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_void_p],
     "sipg_apply_divdiv_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "sipg_project_divdiv_f64": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_void_p,

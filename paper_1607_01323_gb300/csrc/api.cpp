@@ -42,6 +42,7 @@ Mesh::~Mesh() {
   if (dCdf) cudaFree(dCdf);
   if (dconv64) cudaFree(dconv64);
   if (dconvdf) cudaFree(dconvdf);
+  if (dns64) cudaFree(dns64);
   for (auto& pr : pending) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
@@ -120,7 +121,6 @@ void prof_end(Mesh& m, cudaStream_t s, cudaEvent_t e0) {
 
 using namespace sipg;
 
-struct sipg_mesh : public Mesh {};
 
 namespace {
 

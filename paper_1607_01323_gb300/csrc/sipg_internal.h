@@ -92,6 +92,12 @@ struct Mesh {
   std::vector<double> hconv;
   double* dconv64 = nullptr;
   dfl* dconvdf = nullptr;
+  // wall tables of the dual-splitting step (stepper.cu): header S, D, d0, d1,
+  // w (Gauss k+1), then per direction (from ns_off[d]) and layer: J at the
+  // Gauss points, J at both ends, Dv = M^-1 C^T
+  std::vector<double> hns;
+  long long ns_off[3] = {0, 0, 0};
+  double* dns64 = nullptr;
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
   int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
@@ -228,3 +234,7 @@ int default_cpb_plane(int p);
 int cells_per_block(const Mesh& m, int precision);  // current setting or default for the mapping
 
 }  // namespace sipg
+
+// The opaque handle of the C ABI is the mesh itself.
+struct sipg_mesh : public sipg::Mesh {};
+

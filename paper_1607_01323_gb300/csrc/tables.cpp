@@ -328,6 +328,46 @@ int build_tables(Mesh& m) {
       }
     }
   }
+  // wall tables of the dual-splitting step: S, D (Gauss k+1), the end
+  // derivatives d0, d1 and the Gauss weights; per direction and layer the map
+  // derivative J at the Gauss points and both ends, and Dv = M^-1 C^T, the
+  // cell-wise L2 projection of a derivative along that direction (the other
+  // two directions' mass matrices cancel against the inverse mass).
+  {
+    m.hns.clear();
+    m.hns.insert(m.hns.end(), S.begin(), S.end());
+    m.hns.insert(m.hns.end(), D.begin(), D.end());
+    m.hns.insert(m.hns.end(), d0.begin(), d0.end());
+    m.hns.insert(m.hns.end(), d1.begin(), d1.end());
+    m.hns.insert(m.hns.end(), wq.begin(), wq.end());
+    for (int dir = 0; dir < 3; ++dir) {
+      m.ns_off[dir] = (long long)m.hns.size();
+      const int n = m.desc.n[dir];
+      for (int i = 0; i < n; ++i) {
+        std::vector<long double> X(p);
+        for (int a = 0; a < p; ++a) X[a] = map_coord(m.desc, dir, (i + zn[a]) / n);
+        long double J0 = 0.0L, J1 = 0.0L;
+        for (int q = 0; q < p; ++q) {
+          long double J = 0.0L;
+          for (int a = 0; a < p; ++a) J += X[a] * D[q * p + a];
+          m.hns.push_back((double)J);
+        }
+        for (int a = 0; a < p; ++a) {
+          J0 += X[a] * d0[a];
+          J1 += X[a] * d1[a];
+        }
+        m.hns.push_back((double)J0);
+        m.hns.push_back((double)J1);
+        const double* Mi = &m.htab[dir][(size_t)i * lstride(p) + lay_Mi(p)];
+        for (int a = 0; a < p; ++a)
+          for (int b = 0; b < p; ++b) {
+            long double v = 0.0L;
+            for (int c = 0; c < p; ++c) v += (long double)Mi[a * p + c] * m.hC[b * p + c];
+            m.hns.push_back((double)v);
+          }
+      }
+    }
+  }
   // upload (double, float and double-float copies)
   {
     if (m.dC64) cudaFree(m.dC64);
@@ -358,6 +398,11 @@ int build_tables(Mesh& m) {
       e = cudaMemcpy(m.dconv64, m.hconv.data(), m.hconv.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&m.dconvdf, cvd.size() * sizeof(dfl));
     if (e == cudaSuccess) e = cudaMemcpy(m.dconvdf, cvd.data(), cvd.size() * sizeof(dfl), cudaMemcpyHostToDevice);
+    if (m.dns64) cudaFree(m.dns64);
+    m.dns64 = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&m.dns64, m.hns.size() * sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(m.dns64, m.hns.data(), m.hns.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload derivative-mass table");
   }
   for (int dir = 0; dir < 3; ++dir) {
