@@ -528,7 +528,8 @@ def run_config(args):
         versus plain FP64 Jacobi CG;
     c5: adjoint gradient on the 32^3 k=3 channel with per-cell viscosity;
     v3c: divergence, gradient, tau_D and the div-div local projection of the
-        pressure-projection step on the 32^3 k=4 channel."""
+        pressure-projection step on the 32^3 k=4 channel;
+    ns: the dual-splitting time step (BDF3, V3c) on the 32^3 k=4 channel."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -640,6 +641,36 @@ def run_config(args):
         out["backward_over_forward"] = (t_fb - t_f) / t_f
         out["finite_difference_estimate_s"] = 2 * m.ncell * t_f
         out["grad_norm"] = torch.linalg.norm(g).item()
+    elif args.workload == "ns":
+        # the dual-splitting step on the bench channel: laminar profile plus
+        # noise, body force 2 nu, BDF3, div-div penalty, GMG pressure solve;
+        # relative tolerances 1e-6 with extrapolated initial guesses (Sec. 5.1)
+        from paper_1607_01323_gb300 import NavierStokes
+        nu, dt = 1 / 180, 1e-3
+        n_ns = (args.cells,) * 3 if args.cells else w["n"]
+        ns = NavierStokes(n_ns, w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"],
+                          k=w["k"], nu=nu, dt=dt, order=3, zeta=1.0, pressure_precond="gmg_f32", rtol_pressure=1e-6,
+                          rtol_viscous=1e-6, rtol_projection=1e-8, f64_arithmetic=args.f64)
+        N = ns.n_dofs
+        X = ns.velocity_mesh.node_coordinates()
+        u0 = np.concatenate([(1 - X[:, 1] ** 2) * (1 + 0.1 * inputs.normal(0, "ux", N)),
+                             0.1 * (1 - X[:, 1] ** 2) * inputs.normal(0, "uy", N),
+                             0.1 * (1 - X[:, 1] ** 2) * inputs.normal(0, "uz", N)])
+        ns.set_velocity(torch.tensor(u0, device="cuda"))
+        f = (2 * nu, 0.0, 0.0)
+        stats = [ns.step(f) for _ in range(max(args.warmup, 3))]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = [ns.step(f) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        t = (time.perf_counter() - t0) / args.steps
+        mean = lambda key: float(np.mean([st_[key] for st_ in stats]))
+        out["dual_splitting_step"] = {
+            "mesh": "%dx%dx%d tanh channel, k=%d" % (tuple(n_ns) + (w["k"],)), "velocity_dofs": 3 * N,
+            "ms_per_step": 1e3 * t, "velocity_dof_steps_per_s": 3 * N / t, "steps_timed": args.steps,
+            "pressure_iters": mean("pressure_iters"), "viscous_iters": mean("viscous_iters"),
+            "projection_max_cell_iters": mean("projection_iters"), "nu": nu, "dt": dt, "order": 3,
+            "rtol_pressure_viscous": 1e-6}
     elif args.workload == "v3c":
         # the pressure-projection neighbours of the Poisson solve (variant V3c)
         # on the 32^3 k=4 channel: divergence rhs, pressure gradient, tau_D
@@ -689,8 +720,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--f64", default="double_float", choices=["native", "double_float"],
                     help="arithmetic of the FP64 operator (double_float: FP32 pairs on the FP32 pipes)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "v3c"],
-                    help="c2 (default) is the bench step; c3-c5 print timings of the other configurations")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "v3c", "ns"],
+                    help="c2 (default) is the bench step; c1, c3-c5, v3c, ns print timings of other workloads")
     args = ap.parse_args()
     if args.mode == "apply":
         run_apply_only(args)

@@ -349,6 +349,9 @@ int sipg_apply_convective_f64(const sipg_mesh* mesh, const double* u, double* y,
  *        of Eq. (bv3) and tau_D of Eq. (tauD) from u^n (per-cell CG);
  *  (iv)  ((gamma0/dt) M + A_nu) u^(n+1) = (gamma0/dt) M u_hathat with the
  *        divergence-form viscous operator (M^-1-preconditioned CG).
+ * The pressure and viscous CG start from the order-J extrapolations
+ * sum beta_i p^(n-i) and sum beta_i u^(n-i) (Sec. 5.1), so that low relative
+ * tolerances still give accurate solutions.
  * Velocity boundaries: periodic sides and no-slip walls (SIPG_BC_DIRICHLET,
  * g_u = 0); SIPG_BC_NEUMANN (outflow) sides are rejected.  Until `order`
  * levels are known the order rises one step at a time. */

@@ -275,7 +275,11 @@ struct sipg_ns {
   int lev[3] = {0, 1, 2};
   int nlev = 0;
   double *uhat = nullptr, *uhh = nullptr, *t1 = nullptr, *t2 = nullptr;
-  double *rhs_p = nullptr, *p = nullptr, *tau = nullptr;
+  double *rhs_p = nullptr, *tau = nullptr;
+  // pressure history for the extrapolated initial guess (Sec. 5.1)
+  double* pr[3] = {nullptr, nullptr, nullptr};
+  int plev[3] = {0, 1, 2};
+  int npl = 0;
   int *dwcell = nullptr, *dwmask = nullptr, *dwfirst = nullptr;
   int nw = 0, nwf = 0;
   std::vector<void*> owned;
@@ -430,7 +434,8 @@ int sipg_ns_create(const sipg_mesh_desc* desc, const sipg_ns_params* prm, sipg_n
   }
   if ((st = ns_alloc(*ns, (void**)&ns->uhat, V)) || (st = ns_alloc(*ns, (void**)&ns->uhh, V)) ||
       (st = ns_alloc(*ns, (void**)&ns->t1, V)) || (st = ns_alloc(*ns, (void**)&ns->t2, V)) ||
-      (st = ns_alloc(*ns, (void**)&ns->rhs_p, S)) || (st = ns_alloc(*ns, (void**)&ns->p, S)) ||
+      (st = ns_alloc(*ns, (void**)&ns->rhs_p, S)) || (st = ns_alloc(*ns, (void**)&ns->pr[0], S)) ||
+      (st = ns_alloc(*ns, (void**)&ns->pr[1], S)) || (st = ns_alloc(*ns, (void**)&ns->pr[2], S)) ||
       (st = ns_alloc(*ns, (void**)&ns->tau, (size_t)ns->mv->ncell * sizeof(double))) ||
       (st = ns_alloc(*ns, (void**)&ns->dwcell, wc.size() * sizeof(int))) ||
       (st = ns_alloc(*ns, (void**)&ns->dwmask, wm.size() * sizeof(int))) ||
@@ -476,7 +481,11 @@ int sipg_ns_set_velocity(sipg_ns* ns, int level, const double* u, void* stream) 
   if (e != cudaSuccess) return cuda_fail(e, "copy velocity");
   ns->nlev = level + 1;
   if ((st = ns_level_terms(*ns, slot, s))) return st;
-  if (level == 0) cudaMemsetAsync(ns->p, 0, (size_t)ns->N * sizeof(double), s);
+  if (level == 0) {
+    ns->npl = 0;
+    for (int i = 0; i < 3; ++i) ns->plev[i] = i;
+    cudaMemsetAsync(ns->pr[0], 0, (size_t)ns->N * sizeof(double), s);
+  }
   e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "set velocity");
 }
@@ -531,12 +540,25 @@ int sipg_ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stat
   po.maxit = q.maxit;
   int pit = 0, vit = 0, jit = 0;
   double prr = 0.0, vrr = 0.0;
-  const int pst = sipg_cg_solve(ns->mp, &po, ns->rhs_p, ns->p, 1, s, &pit, &prr);
+  // initial guess: the pressure extrapolated with the beta of the order the
+  // known pressure levels allow (Sec. 5.1)
+  const int Jp = ns->npl < J ? ns->npl : J;
+  const int new_p = ns->npl < q.order ? ns->plev[ns->npl] : ns->plev[q.order - 1];
+  if (Jp > 0) {
+    double gp, ap[3], bp[3];
+    bdf_ex(Jp, gp, ap, bp);
+    const double* x[3];
+    for (int i = 0; i < Jp; ++i) x[i] = ns->pr[ns->plev[i]];
+    if ((st = ns_lincomb(*ns, N, Jp, x, bp, nullptr, ns->pr[new_p], s))) return st;
+  } else {
+    cudaMemsetAsync(ns->pr[new_p], 0, (size_t)N * sizeof(double), s);
+  }
+  const int pst = sipg_cg_solve(ns->mp, &po, ns->rhs_p, ns->pr[new_p], 1, s, &pit, &prr);
   if (pst != SIPG_OK && pst != SIPG_MAXITER) return pst;
   // (iii) projection: (M + tau_D B) u_hathat = M u_hat + (dt/gamma0) G p
   if ((st = sipg_tau_div_f64(ns->mv, ns->u[ns->lev[0]], q.zeta, dt, ns->tau, s))) return st;
   if ((st = sipg_apply_mass_f64(ns->mv, ns->uhat, ns->t1, 3, s))) return st;
-  if ((st = sipg_apply_gradient_f64(ns->mv, ns->p, ns->t2, s))) return st;
+  if ((st = sipg_apply_gradient_f64(ns->mv, ns->pr[new_p], ns->t2, s))) return st;
   {
     const double* x[2] = {ns->t1, ns->t2};
     const double c[2] = {1.0, dt / g0};
@@ -557,8 +579,13 @@ int sipg_ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stat
   // a free slot while fewer than `order` levels are known, else the oldest
   // level's (its data were last used in (ii))
   const int new_slot = (ns->nlev < q.order) ? ns->lev[ns->nlev] : ns->lev[q.order - 1];
-  e = cudaMemcpyAsync(ns->u[new_slot], ns->uhh, (size_t)N3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(e, "copy u_hathat");
+  {
+    // initial guess: the velocity extrapolated with beta (Sec. 5.1); the slot
+    // may hold the oldest level, read and overwritten element by element
+    const double* x[3];
+    for (int i = 0; i < J; ++i) x[i] = ns->u[ns->lev[i]];
+    if ((st = ns_lincomb(*ns, N3, J, x, be, nullptr, ns->u[new_slot], s))) return st;
+  }
   sipg_cg_opts vo;
   sipg_cg_default_opts(&vo);
   vo.op = SIPG_OP_VISCOUS;
@@ -577,6 +604,12 @@ int sipg_ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stat
     if (ns->lev[i] != new_slot) nl[w++] = ns->lev[i];
   for (int i = 0; i < 3; ++i) ns->lev[i] = nl[i];
   ns->nlev = keep;
+  int pl[3] = {new_p, 0, 0};
+  w = 1;
+  for (int i = 0; i < 3 && w < 3; ++i)
+    if (ns->plev[i] != new_p) pl[w++] = ns->plev[i];
+  for (int i = 0; i < 3; ++i) ns->plev[i] = pl[i];
+  ns->npl = ns->npl < q.order ? ns->npl + 1 : q.order;
   if ((st = ns_level_terms(*ns, new_slot, s))) return st;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "step");
@@ -608,8 +641,8 @@ int sipg_ns_pressure(const sipg_ns* ns, double* p, void* stream) {
   if (!ns || !p) return fail(SIPG_EINVAL, "NULL argument");
   int st;
   if ((st = ns_device(*ns))) return st;
-  const cudaError_t e = cudaMemcpyAsync(p, ns->p, (size_t)ns->N * sizeof(double), cudaMemcpyDeviceToDevice,
-                                        (cudaStream_t)stream);
+  const cudaError_t e = cudaMemcpyAsync(p, ns->pr[ns->plev[0]], (size_t)ns->N * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "copy pressure");
 }
 
