@@ -222,44 +222,44 @@ __device__ void cell_chain(const CellCtxT<T>& cc, const T* const (&A)[3], const 
 }
 
 // y = (M + tau B) u on one cell: u, y: [3][P3]
-template <int P>
-__device__ void divdiv_cell(const CellCtx& cc, double tau, const double* u, double* y, double* t1, double* t2) {
+template <int P, typename T>
+__device__ void divdiv_cell(const CellCtxT<T>& cc, T tau, const T* u, T* y, T* t1, T* t2) {
   using O = LayerOff<P>;
   constexpr int P3 = P * P * P;
-  const double* Mr[3] = {cc.L[0] + O::M, cc.L[1] + O::M, cc.L[2] + O::M};
-  const double* Kr[3] = {cc.L[0] + O::K, cc.L[1] + O::K, cc.L[2] + O::K};
+  const T* Mr[3] = {cc.L[0] + O::M, cc.L[1] + O::M, cc.L[2] + O::M};
+  const T* Kr[3] = {cc.L[0] + O::K, cc.L[1] + O::K, cc.L[2] + O::K};
   for (int d = 0; d < 3; ++d) {
     // diagonal block: (M_d + tau K_d) along d, M along the others
     {
-      const double* A[3] = {Mr[0], Mr[1], Mr[2]};
-      const double* B[3] = {nullptr, nullptr, nullptr};
-      double cB[3] = {0.0, 0.0, 0.0};
+      const T* A[3] = {Mr[0], Mr[1], Mr[2]};
+      const T* B[3] = {nullptr, nullptr, nullptr};
+      T cB[3] = {T(0), T(0), T(0)};
       B[d] = Kr[d];
       cB[d] = tau;
-      cell_chain<P>(cc, A, B, cB, u + d * P3, y + d * P3, t1, t2, 0, 1.0);
+      cell_chain<P>(cc, A, B, cB, u + d * P3, y + d * P3, t1, t2, 0, T(1));
     }
     // off-diagonal blocks: C along d (test derivative), C^T along d' (trial derivative)
     for (int dp = 0; dp < 3; ++dp) {
       if (dp == d) continue;
-      const double* A[3] = {Mr[0], Mr[1], Mr[2]};
+      const T* A[3] = {Mr[0], Mr[1], Mr[2]};
       A[d] = cc.C;
       A[dp] = cc.Ct;
-      const double* B[3] = {nullptr, nullptr, nullptr};
-      const double cB[3] = {0.0, 0.0, 0.0};
+      const T* B[3] = {nullptr, nullptr, nullptr};
+      const T cB[3] = {T(0), T(0), T(0)};
       cell_chain<P>(cc, A, B, cB, u + dp * P3, y + d * P3, t1, t2, 1, tau);
     }
   }
 }
 
 // z = M^-1 r per component (tensorial inverse mass, Sec. 5)
-template <int P>
-__device__ void invmass_cell(const CellCtx& cc, const double* r, double* z, double* t1, double* t2) {
+template <int P, typename T>
+__device__ void invmass_cell(const CellCtxT<T>& cc, const T* r, T* z, T* t1, T* t2) {
   using O = LayerOff<P>;
   constexpr int P3 = P * P * P;
-  const double* A[3] = {cc.L[0] + O::Mi, cc.L[1] + O::Mi, cc.L[2] + O::Mi};
-  const double* B[3] = {nullptr, nullptr, nullptr};
-  const double cB[3] = {0.0, 0.0, 0.0};
-  for (int d = 0; d < 3; ++d) cell_chain<P>(cc, A, B, cB, r + d * P3, z + d * P3, t1, t2, 0, 1.0);
+  const T* A[3] = {cc.L[0] + O::Mi, cc.L[1] + O::Mi, cc.L[2] + O::Mi};
+  const T* B[3] = {nullptr, nullptr, nullptr};
+  const T cB[3] = {T(0), T(0), T(0)};
+  for (int d = 0; d < 3; ++d) cell_chain<P>(cc, A, B, cB, r + d * P3, z + d * P3, t1, t2, 0, T(1));
 }
 
 // sum of v over the block (blockDim <= 1024), result broadcast to all threads
@@ -320,86 +320,91 @@ __global__ void divdiv_apply_kernel(Geo<double> g, const double* __restrict__ Cg
 
 // Per-cell CG on (M + tau B) x = rhs with z = M^-1 r; x holds the initial
 // guess.  status[0] |= 1 if a cell stops at maxit, |= 2 on breakdown;
-// status[1] = max iterations over the cells.
-template <int P>
-__global__ void divdiv_solve_kernel(Geo<double> g, const double* __restrict__ Cg, const double* __restrict__ tau,
+// status[1] = max iterations over the cells.  T = double or dfl: the vectors
+// and contractions in T, the dot products summed per thread in T and over the
+// block in FP64, the CG scalars in FP64.
+template <typename T, int P>
+__global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const double* __restrict__ tau,
                                     const double* __restrict__ rhs, double* __restrict__ x, double rtol, int maxit,
                                     int* __restrict__ status) {
   constexpr int P3 = P * P * P, V = 3 * P3;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* sx = reinterpret_cast<double*>(smraw);
-  double* sr = sx + V;
-  double* sp = sr + V;
-  double* sq = sp + V;  // A p, and after the updates z = M^-1 r (one buffer)
-  double* sz = sq;
-  double* t1 = sq + V;
-  double* t2 = t1 + P3;
-  double* C = t2 + P3;
-  double* Ct = C + P * P;
-  double* red = Ct + P * P;  // 32
+  T* sx = reinterpret_cast<T*>(smraw);
+  T* sr = sx + V;
+  T* sp = sr + V;
+  T* sq = sp + V;  // A p, and after the updates z = M^-1 r (one buffer)
+  T* sz = sq;
+  T* t1 = sq + V;
+  T* t2 = t1 + P3;
+  T* C = t2 + P3;
+  T* Ct = C + P * P;
+  double* red = reinterpret_cast<double*>(Ct + P * P);  // 32
   const int e = blockIdx.x;
   const long long N = (long long)g.ncell * P3;
   double bb = 0.0;
   for (int i = threadIdx.x; i < V; i += blockDim.x) {
     const long long gi = (i / P3) * N + (long long)e * P3 + i % P3;
-    sx[i] = x[gi];
-    sr[i] = rhs[gi];
-    bb += sr[i] * sr[i];
+    sx[i] = cvt_in<T, double>(x[gi]);
+    const double b = rhs[gi];
+    sr[i] = cvt_in<T, double>(b);
+    bb += b * b;
   }
   stage_c<P>(Cg, C, Ct);
   __syncthreads();
   bb = block_sum(bb, red);
-  const CellCtx cc = cell_ctx<P>(g, e, C, Ct);
-  const double te = tau[e];
+  const CellCtxT<T> cc = cell_ctx<P>(g, e, (const T*)C, (const T*)Ct);
+  const T te = cvt_in<T, double>(tau[e]);
   // r = rhs - A x
   divdiv_cell<P>(cc, te, sx, sq, t1, t2);
-  double rr = 0.0;
+  T acc = T(0);
   for (int i = threadIdx.x; i < V; i += blockDim.x) {
-    sr[i] -= sq[i];
-    rr += sr[i] * sr[i];
+    sr[i] = sr[i] - sq[i];
+    acc = fma(sr[i], sr[i], acc);
   }
   __syncthreads();
-  rr = block_sum(rr, red);
+  double rr = block_sum(cvt_out<double, T>(acc), red);
   invmass_cell<P>(cc, sr, sz, t1, t2);
-  double rz = 0.0;
+  acc = T(0);
   for (int i = threadIdx.x; i < V; i += blockDim.x) {
     sp[i] = sz[i];
-    rz += sr[i] * sz[i];
+    acc = fma(sr[i], sz[i], acc);
   }
   __syncthreads();
-  rz = block_sum(rz, red);
+  double rz = block_sum(cvt_out<double, T>(acc), red);
   const double tol2 = rtol * rtol * bb;
   int it = 0;
   bool broke = false;
   while (rr > tol2 && it < maxit) {
     divdiv_cell<P>(cc, te, sp, sq, t1, t2);
-    double pq = 0.0;
-    for (int i = threadIdx.x; i < V; i += blockDim.x) pq += sp[i] * sq[i];
-    pq = block_sum(pq, red);
+    acc = T(0);
+    for (int i = threadIdx.x; i < V; i += blockDim.x) acc = fma(sp[i], sq[i], acc);
+    const double pq = block_sum(cvt_out<double, T>(acc), red);
     if (!(pq > 0.0)) {
       broke = true;
       break;
     }
     const double alpha = rz / pq;
-    rr = 0.0;
+    const T ap = cvt_in<T, double>(alpha), am = cvt_in<T, double>(-alpha);
+    acc = T(0);
     for (int i = threadIdx.x; i < V; i += blockDim.x) {
-      sx[i] = fma(alpha, sp[i], sx[i]);
-      sr[i] = fma(-alpha, sq[i], sr[i]);
-      rr += sr[i] * sr[i];
+      sx[i] = fma(ap, sp[i], sx[i]);
+      sr[i] = fma(am, sq[i], sr[i]);
+      acc = fma(sr[i], sr[i], acc);
     }
     __syncthreads();
-    rr = block_sum(rr, red);
+    rr = block_sum(cvt_out<double, T>(acc), red);
     invmass_cell<P>(cc, sr, sz, t1, t2);
-    double rzn = 0.0;
-    for (int i = threadIdx.x; i < V; i += blockDim.x) rzn += sr[i] * sz[i];
-    rzn = block_sum(rzn, red);
-    const double beta = rzn / rz;
+    acc = T(0);
+    for (int i = threadIdx.x; i < V; i += blockDim.x) acc = fma(sr[i], sz[i], acc);
+    const double rzn = block_sum(cvt_out<double, T>(acc), red);
+    const T bt = cvt_in<T, double>(rzn / rz);
     rz = rzn;
-    for (int i = threadIdx.x; i < V; i += blockDim.x) sp[i] = fma(beta, sp[i], sz[i]);
+    for (int i = threadIdx.x; i < V; i += blockDim.x) sp[i] = fma(bt, sp[i], sz[i]);
     __syncthreads();
     ++it;
   }
-  for (int i = threadIdx.x; i < V; i += blockDim.x) x[(i / P3) * N + (long long)e * P3 + i % P3] = sx[i];
+  for (int i = threadIdx.x; i < V; i += blockDim.x)
+    x[(i / P3) * N + (long long)e * P3 + i % P3] = cvt_out<double, T>(sx[i]);
   if (threadIdx.x == 0) {
     if (broke) atomicOr(status, 2);
     else if (rr > tol2) atomicOr(status, 1);
@@ -637,13 +642,21 @@ int launch_divdiv_solve_p(const Mesh& m, const double* tau, const double* rhs, d
                           int* status, cudaStream_t s) {
   constexpr int P3 = P * P * P;
   const size_t smem = (size_t)(12 * P3 + 2 * P3 + 2 * P * P + 32) * sizeof(double);
+  const bool df = m.f64_arith == SIPG_F64_DOUBLE_FLOAT;
   cudaError_t e;
-  if (smem > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(divdiv_solve_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-          cudaSuccess)
-    return cuda_fail(e, "cudaFuncSetAttribute(div-div solve)");
-  divdiv_solve_kernel<P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<double>(m), m.dC64, tau, rhs, x,
-                                                                          rtol, maxit, status);
+  if (smem > 48 * 1024) {
+    e = df ? cudaFuncSetAttribute(divdiv_solve_kernel<dfl, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)
+           : cudaFuncSetAttribute(divdiv_solve_kernel<double, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(div-div solve)");
+  }
+  if (df)
+    divdiv_solve_kernel<dfl, P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<dfl>(m), m.dCdf, tau,
+                                                                                 rhs, x, rtol, maxit, status);
+  else
+    divdiv_solve_kernel<double, P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<double>(m), m.dC64, tau,
+                                                                                    rhs, x, rtol, maxit, status);
   const_cast<Mesh&>(m).launches++;
   e = cudaGetLastError();
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "div-div solve launch");

@@ -84,6 +84,11 @@ def test_tau_divdiv_apply_and_solve(name, c, k):
     x = x.cpu().numpy()
     assert np.abs(x - x_ref).max() <= 1e-10 * np.abs(x_ref).max()
     assert 1 <= iters <= 3 * (k + 1) ** 3
+    # the local solve in double-float arithmetic: same solution to the tolerance
+    m.set_f64_arithmetic("double_float")
+    x2, iters2 = project_divdiv_f64(m, _cuda(tau_ref), _cuda(rhs), rtol=1e-12, maxit=500)
+    assert np.abs(x2.cpu().numpy() - x_ref).max() <= 1e-9 * np.abs(x_ref).max()
+    assert abs(iters2 - iters) <= 3 + iters // 4
 
 
 def test_projection_reduces_divergence_and_keeps_free_fields():
