@@ -445,16 +445,6 @@ __global__ void k_dot_sink(const int* __restrict__ skip, long long n, const doub
   }
 }
 
-// r.r partials only (for separately formed z)
-__global__ void k_dot_rr(const Scalars* __restrict__ sc, long long n, const double* __restrict__ r,
-                         double* __restrict__ part) {
-  double rr = 0.0;
-  if (!sc->done)
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-      rr += r[i] * r[i];
-  block_partial3(rr, 0.0, 0.0, part);
-}
-
 // ------------------------------------------------------- FP32 Chebyshev
 // start: r32 = (float) r; d = D^-1 r32 / theta; x32 = d
 __global__ void k_cheb_start(const Scalars* __restrict__ sc, long long n, const double* __restrict__ r,
@@ -665,7 +655,6 @@ struct Solver {
       sink.skip = &w.sc->done;
       sink.sums = o.zero_mean ? 1 : 0;
     }
-    cudaEvent_t e0 = nullptr;
     if (m.profile) {
       if (ev_used >= (int)evs.size()) {
         std::pair<cudaEvent_t, cudaEvent_t> pr;
