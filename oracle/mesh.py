@@ -7,6 +7,10 @@
   the cell's Gauss-Lobatto nodes.
 * Sec. 7.1: the channel grading x_2 -> delta tanh(gamma (2 x_2 - 1)) / tanh(gamma)
   of the wall-normal coordinate (here scaled to [lo_y, hi_y]).
+* "perturbed": the box plus a seeded smooth displacement that vanishes on the
+  box boundary (a non-separable map for general-metric tests; not in the
+  paper, which treats general curved meshes through the same iso-parametric
+  mapping).
 
 Cells are numbered lexicographically, x fastest: cell = (iz * ny + iy) * nx + ix.
 Nodes inside a cell are numbered i = (c * p + b) * p + a with a along x.
@@ -29,8 +33,10 @@ class MeshSpec:
     hi: tuple = (1.0, 1.0, 1.0)
     bc_lo: tuple = (PERIODIC, PERIODIC, PERIODIC)
     bc_hi: tuple = (PERIODIC, PERIODIC, PERIODIC)
-    mapping: str = "affine"  # "affine", "channel", or "channel_linear"
+    mapping: str = "affine"  # "affine", "channel", "channel_linear" or "perturbed"
     gamma: float = 1.8
+    amplitude: float = 0.0   # "perturbed": size of the displacement relative to the box
+    seed: int = 0            # "perturbed": selects the displacement's coefficients
     n: tuple = field(init=False)
 
     def __post_init__(self):
@@ -63,9 +69,30 @@ def analytic_map(spec, s):
         y1 = np.tanh(g * (2.0 * e1 - 1.0)) / np.tanh(g)
         t = y0 + (y1 - y0) * (s[..., 1] - e0) * ny
         x[..., 1] = lo[1] + (hi[1] - lo[1]) * 0.5 * (1.0 + t)
+    elif spec.mapping == "perturbed":
+        x = x + perturbation(spec, s)
     elif spec.mapping != "affine":
         raise ValueError("unknown mapping " + spec.mapping)
     return x
+
+
+def perturbation_coefficients(seed):
+    """c_i in [-1, 1] from 16-bit fields of the seed: c_i = 2 f_i / 65535 - 1."""
+    return np.array([2.0 * ((int(seed) >> (16 * i)) & 0xFFFF) / 65535.0 - 1.0 for i in range(3)])
+
+
+def perturbation(spec, s):
+    """A smooth displacement that vanishes on the box boundary and couples the
+    directions (a general, non-separable map for general-metric tests):
+        w_i = amplitude (hi_i - lo_i) c_i b(s) cos(pi (s_(i+1) - s_(i+2))),
+        b(s) = sin(pi s_x) sin(pi s_y) sin(pi s_z)."""
+    c = perturbation_coefficients(spec.seed)
+    L = np.asarray(spec.hi, dtype=np.float64) - np.asarray(spec.lo, dtype=np.float64)
+    b = np.sin(np.pi * s[..., 0]) * np.sin(np.pi * s[..., 1]) * np.sin(np.pi * s[..., 2])
+    w = np.zeros_like(s)
+    for i in range(3):
+        w[..., i] = spec.amplitude * L[i] * c[i] * b * np.cos(np.pi * (s[..., (i + 1) % 3] - s[..., (i + 2) % 3]))
+    return w
 
 
 def cell_index(spec, ix, iy, iz):
