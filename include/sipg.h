@@ -58,7 +58,12 @@ typedef enum {
 } sipg_status;
 
 typedef enum { SIPG_BC_PERIODIC = 0, SIPG_BC_DIRICHLET = 1, SIPG_BC_NEUMANN = 2 } sipg_bc;
-typedef enum { SIPG_MAP_AFFINE = 0, SIPG_MAP_CHANNEL_TANH = 1, SIPG_MAP_CHANNEL_LINEAR = 2 } sipg_map;
+typedef enum {
+  SIPG_MAP_AFFINE = 0,
+  SIPG_MAP_CHANNEL_TANH = 1,
+  SIPG_MAP_CHANNEL_LINEAR = 2,
+  SIPG_MAP_PERTURBED = 3
+} sipg_map;
 /* SIPG_OP_VISCOUS: mass_coef M + the divergence-form viscous operator of
  * sipg_apply_viscous_f64 (3 coupled components; CG with SIPG_PC_NONE or
  * SIPG_PC_INVMASS). */
@@ -82,7 +87,17 @@ typedef enum {
  * (Sec. 7.1 with delta = 1 for lo=-1, hi=1); x and z stay affine.
  * map = SIPG_MAP_CHANNEL_LINEAR takes the same y at the cell boundaries
  * eta_j = j / n[1] and is affine inside each cell (straight cells on the
- * graded vertices; the coarse levels of the multigrid hierarchy). */
+ * graded vertices; the coarse levels of the multigrid hierarchy).
+ * map = SIPG_MAP_PERTURBED is the box plus a smooth displacement that vanishes
+ * on the box boundary (general, non-separable metrics):
+ *   x_i += amplitude (hi_i - lo_i) c_i b(s) cos(pi (s_(i+1) - s_(i+2))),
+ *   b(s) = sin(pi s_x) sin(pi s_y) sin(pi s_z), s the global reference
+ *   coordinate in [0,1]^3, c_i = 2 f_i / 65535 - 1 with f_i the 16-bit field
+ *   i of seed.
+ * Its geometry is stored per quadrature point (56 B per DoF plus face data);
+ * it supports the FP64 Laplace / Helmholtz / mass applies with a constant
+ * viscosity and sipg_cg_solve with SIPG_PC_NONE; the other entry points need
+ * a separable map and return SIPG_EINVAL. */
 typedef struct {
   int n[3];          /* cells per direction, each >= 1                         */
   double lo[3];      /* box corner                                             */
@@ -91,6 +106,8 @@ typedef struct {
   int bc_hi[3];
   int map;           /* sipg_map                                               */
   double gamma;      /* grading parameter (> 0) for SIPG_MAP_CHANNEL_TANH       */
+  double amplitude;  /* SIPG_MAP_PERTURBED: displacement size (>= 0)          */
+  unsigned long long seed; /* SIPG_MAP_PERTURBED: displacement coefficients  */
 } sipg_mesh_desc;
 
 /* Create a mesh on the current CUDA device.  The degree defaults to k = 3 and

@@ -55,9 +55,10 @@ class Mesh:
     penalty: factor on tau of Eq. (taue)."""
 
     def __init__(self, n, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc_lo=("periodic",) * 3,
-                 bc_hi=("periodic",) * 3, mapping="affine", gamma=1.8, k=3, penalty=1.0):
+                 bc_hi=("periodic",) * 3, mapping="affine", gamma=1.8, k=3, penalty=1.0, amplitude=0.0, seed=0):
         lib = L.lib()
         d = L.MeshDesc()
+        d.amplitude, d.seed = float(amplitude), int(seed)
         for i in range(3):
             d.n[i] = int(n[i])
             d.lo[i] = float(lo[i])

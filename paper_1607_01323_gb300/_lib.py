@@ -7,14 +7,15 @@ LIB_PATH = os.path.join(HERE, "libsipg.so")
 
 OK, MAXITER, EINVAL, ECUDA, ENOMEM, BREAKDOWN, NONFINITE = 0, 1, -1, -2, -3, -4, -5
 BC = {"periodic": 0, "dirichlet": 1, "neumann": 2}
-MAP = {"affine": 0, "channel": 1, "channel_linear": 2}
+MAP = {"affine": 0, "channel": 1, "channel_linear": 2, "perturbed": 3}
 OP = {"laplace": 0, "helmholtz": 1, "viscous": 2}
 PC = {"none": 0, "jacobi": 1, "invmass": 2, "cheb_f32": 3, "gmg_f32": 4}
 
 
 class MeshDesc(C.Structure):
     _fields_ = [("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("bc_lo", C.c_int * 3),
-                ("bc_hi", C.c_int * 3), ("map", C.c_int), ("gamma", C.c_double)]
+                ("bc_hi", C.c_int * 3), ("map", C.c_int), ("gamma", C.c_double), ("amplitude", C.c_double),
+                ("seed", C.c_ulonglong)]
 
 
 class CgOpts(C.Structure):

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libsipg.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["apply_f64.cu", "apply_f32.cu", "misc.cu", "cg.cu", "mg.cu", "projection.cu", "convective.cu", "stepper.cu", "tables.cpp", "api.cpp"]
+SOURCES = ["apply_f64.cu", "apply_f32.cu", "misc.cu", "cg.cu", "mg.cu", "projection.cu", "convective.cu", "stepper.cu", "general.cu", "tables.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

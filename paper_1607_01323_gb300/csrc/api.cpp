@@ -43,6 +43,8 @@ Mesh::~Mesh() {
   if (dconv64) cudaFree(dconv64);
   if (dconvdf) cudaFree(dconvdf);
   if (dns64) cudaFree(dns64);
+  for (double* q : {dgen_head, dgen_geo, dgen_face, dgen_tau})
+    if (q) cudaFree(q);
   for (auto& pr : pending) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
@@ -131,6 +133,14 @@ int check_mesh(const sipg_mesh* m) {
   return SIPG_OK;
 }
 
+// Entry points built on the separable 1D tables reject the general map.
+int check_separable(const sipg_mesh* m) {
+  int st;
+  if ((st = check_mesh(m))) return st;
+  if (m->general()) return fail(SIPG_EINVAL, "this operation needs a separable map (not SIPG_MAP_PERTURBED)");
+  return SIPG_OK;
+}
+
 int check_vec(const void* x, const void* y, int ncomp) {
   if (!x || !y) return fail(SIPG_EINVAL, "vector pointer is NULL");
   if (ncomp < 1) return fail(SIPG_EINVAL, "ncomp must be >= 1");
@@ -163,6 +173,16 @@ int apply_common(const sipg_mesh* mc, T cm, T nu, const T* nu_cell, bool stiffne
   if ((st = set_device(m))) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0;
+  if (m.general()) {
+    if (!std::is_same<T, double>::value || nu_cell)
+      return fail(SIPG_EINVAL, "a perturbed mesh supports FP64 applies with a constant viscosity only");
+    prof_begin(m, s, &e0);
+    st = launch_general(m, reinterpret_cast<const double*>(x), reinterpret_cast<double*>(y), ncomp, (double)cm,
+                        (double)nu, stiffness, nullptr, s);
+    prof_end(m, s, e0);
+    if (st == SIPG_OK && m.profile) m.prof_applies++;
+    return st;
+  }
   prof_begin(m, s, &e0);
   st = launch_apply<T>(m, x, y, ncomp, cm, nu, nu_cell, stiffness, nullptr, nullptr, s);
   prof_end(m, s, e0);
@@ -187,10 +207,14 @@ int sipg_create_mesh(const sipg_mesh_desc* d, sipg_mesh** out) {
     if ((d->bc_lo[i] == SIPG_BC_PERIODIC) != (d->bc_hi[i] == SIPG_BC_PERIODIC))
       return fail(SIPG_EINVAL, "periodic sides must be paired");
   }
-  if (d->map != SIPG_MAP_AFFINE && d->map != SIPG_MAP_CHANNEL_TANH && d->map != SIPG_MAP_CHANNEL_LINEAR)
+  if (d->map != SIPG_MAP_AFFINE && d->map != SIPG_MAP_CHANNEL_TANH && d->map != SIPG_MAP_CHANNEL_LINEAR &&
+      d->map != SIPG_MAP_PERTURBED)
     return fail(SIPG_EINVAL, "unknown map");
-  if (d->map != SIPG_MAP_AFFINE && !(d->gamma > 0.0 && std::isfinite(d->gamma)))
+  if ((d->map == SIPG_MAP_CHANNEL_TANH || d->map == SIPG_MAP_CHANNEL_LINEAR) &&
+      !(d->gamma > 0.0 && std::isfinite(d->gamma)))
     return fail(SIPG_EINVAL, "channel map needs gamma > 0");
+  if (d->map == SIPG_MAP_PERTURBED && !(d->amplitude >= 0.0 && std::isfinite(d->amplitude)))
+    return fail(SIPG_EINVAL, "perturbed map needs a finite amplitude >= 0");
   long long nc = (long long)d->n[0] * d->n[1] * d->n[2];
   if (nc * 512 >= (1LL << 31) * 8LL) return fail(SIPG_EINVAL, "mesh too large");
   if (nc >= (1LL << 31)) return fail(SIPG_EINVAL, "too many cells");
@@ -292,6 +316,19 @@ int sipg_node_coordinates(const sipg_mesh* m, double* xyz) {
   }
   const int nx = m->desc.n[0], ny = m->desc.n[1];
   long long idx = 0;
+  if (m->general()) {
+    const int* n = m->desc.n;
+    for (long long e = 0; e < m->ncell; ++e) {
+      const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)(e / ((long long)nx * ny));
+      for (int c = 0; c < p; ++c)
+        for (int b = 0; b < p; ++b)
+          for (int a = 0; a < p; ++a, ++idx) {
+            const double s[3] = {(ix + zn[a]) / n[0], (iy + zn[b]) / n[1], (iz + zn[c]) / n[2]};
+            map_point(m->desc, s, xyz + 3 * idx);
+          }
+    }
+    return SIPG_OK;
+  }
   for (long long e = 0; e < m->ncell; ++e) {
     const int ix = (int)(e % nx), iy = (int)((e / nx) % ny), iz = (int)(e / ((long long)nx * ny));
     for (int c = 0; c < p; ++c)
@@ -309,6 +346,10 @@ int sipg_penalty_values(const sipg_mesh* m, double* tau) {
   int st;
   if ((st = check_mesh(m))) return st;
   if (!tau) return fail(SIPG_EINVAL, "NULL output");
+  if (m->general()) {
+    for (long long e = 0; e < m->ncell; ++e) tau[e] = m->htau_gen[(size_t)e];
+    return SIPG_OK;
+  }
   const int p = m->p, nx = m->desc.n[0], ny = m->desc.n[1];
   const double s = m->penalty * (m->k + 1) * (m->k + 1);
   const int st_ = lstride(p);
@@ -344,7 +385,7 @@ int sipg_apply_mass_f64(const sipg_mesh* m, const double* x, double* y, int ncom
 
 int sipg_apply_inverse_mass_f64(const sipg_mesh* mc, const double* x, double* y, int ncomp, void* stream) {
   int st;
-  if ((st = check_mesh(mc))) return st;
+  if ((st = check_separable(mc))) return st;
   if ((st = check_vec(x, y, ncomp))) return st;
   Mesh& m = const_cast<sipg_mesh&>(*mc);
   if ((st = set_device(m))) return st;
@@ -354,7 +395,7 @@ int sipg_apply_inverse_mass_f64(const sipg_mesh* mc, const double* x, double* y,
 int sipg_diagonal_f64(const sipg_mesh* mc, int op, double cm, double nu, const double* nu_cell, double* diag,
                       void* stream) {
   int st;
-  if ((st = check_mesh(mc))) return st;
+  if ((st = check_separable(mc))) return st;
   if (!diag) return fail(SIPG_EINVAL, "diag is NULL");
   if (op != SIPG_OP_LAPLACE && op != SIPG_OP_HELMHOLTZ) return fail(SIPG_EINVAL, "unknown operator");
   Mesh& m = const_cast<sipg_mesh&>(*mc);
@@ -408,6 +449,9 @@ int sipg_cg_solve(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* 
     if (o->zero_mean) return fail(SIPG_EINVAL, "zero_mean applies to the Laplace operator only");
   }
   if (o->precond < SIPG_PC_NONE || o->precond > SIPG_PC_GMG_F32) return fail(SIPG_EINVAL, "unknown preconditioner");
+  if (m->general() && (o->op == SIPG_OP_VISCOUS || o->precond != SIPG_PC_NONE || o->nu_cell))
+    return fail(SIPG_EINVAL, "on a perturbed mesh CG supports the Laplace / Helmholtz operator with a constant nu "
+                             "and SIPG_PC_NONE");
   if (o->precond == SIPG_PC_GMG_F32) {
     if (o->op != SIPG_OP_LAPLACE) return fail(SIPG_EINVAL, "the multigrid preconditioner supports the Laplace operator");
     if (ncomp != 1) return fail(SIPG_EINVAL, "the multigrid preconditioner supports one component");
@@ -454,7 +498,7 @@ int sipg_cg_solve(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* 
 int sipg_cg_solve_noalloc(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* x, int ncomp, void* stream,
                           int* iters, double* relres) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!o) return fail(SIPG_EINVAL, "opts is NULL");
   if ((st = check_vec(b, x, ncomp))) return st;
   if (o->op != SIPG_OP_LAPLACE && o->op != SIPG_OP_HELMHOLTZ) return fail(SIPG_EINVAL, "unknown operator");
@@ -475,7 +519,7 @@ int sipg_cg_solve_noalloc(sipg_mesh* m, const sipg_cg_opts* o, const double* b, 
 
 int sipg_mg_setup(sipg_mesh* m, const sipg_cg_opts* o, void* stream) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!o) return fail(SIPG_EINVAL, "opts is NULL");
   bool all_bc_free = true;
   for (int d = 0; d < 3; ++d)
@@ -496,7 +540,7 @@ int sipg_mg_info(const sipg_mesh* m, int max_levels, int* nlevels, int* n_cells,
 
 int sipg_mg_vcycle(sipg_mesh* m, const double* r, double* z, void* stream) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!r || !z) return fail(SIPG_EINVAL, "NULL vector");
   if (r == z) return fail(SIPG_EINVAL, "r and z must not overlap");
   if (!m->mg) return fail(SIPG_EINVAL, "no multigrid hierarchy set up on this mesh (sipg_mg_setup)");
@@ -506,7 +550,7 @@ int sipg_mg_vcycle(sipg_mesh* m, const double* r, double* z, void* stream) {
 
 int sipg_apply_divergence_f64(const sipg_mesh* m, const double* u, double* y, void* stream) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!u || !y) return fail(SIPG_EINVAL, "NULL vector");
   if (u == y) return fail(SIPG_EINVAL, "u and y must not overlap");
   if ((st = set_device(const_cast<sipg_mesh&>(*m)))) return st;
@@ -515,7 +559,7 @@ int sipg_apply_divergence_f64(const sipg_mesh* m, const double* u, double* y, vo
 
 int sipg_apply_gradient_f64(const sipg_mesh* m, const double* p, double* y, void* stream) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!p || !y) return fail(SIPG_EINVAL, "NULL vector");
   if (p == y) return fail(SIPG_EINVAL, "p and y must not overlap");
   if ((st = set_device(const_cast<sipg_mesh&>(*m)))) return st;
@@ -525,7 +569,7 @@ int sipg_apply_gradient_f64(const sipg_mesh* m, const double* p, double* y, void
 int sipg_apply_viscous_f64(const sipg_mesh* m, double mass_coef, double nu, const double* u, double* y,
                            void* stream) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!u || !y) return fail(SIPG_EINVAL, "NULL vector");
   if (u == y) return fail(SIPG_EINVAL, "u and y must not overlap");
   if (!(mass_coef >= 0.0) || !std::isfinite(mass_coef)) return fail(SIPG_EINVAL, "mass_coef must be finite and >= 0");
@@ -538,7 +582,7 @@ int sipg_apply_viscous_f64(const sipg_mesh* m, double mass_coef, double nu, cons
 
 int sipg_apply_convective_f64(const sipg_mesh* m, const double* u, double* y, void* stream) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!u || !y) return fail(SIPG_EINVAL, "NULL vector");
   if (u == y) return fail(SIPG_EINVAL, "u and y must not overlap");
   if ((st = set_device(*m))) return st;
@@ -547,7 +591,7 @@ int sipg_apply_convective_f64(const sipg_mesh* m, const double* u, double* y, vo
 
 int sipg_tau_div_f64(const sipg_mesh* m, const double* u, double zeta, double dt, double* tau, void* stream) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!u || !tau) return fail(SIPG_EINVAL, "NULL vector");
   if (!(zeta >= 0.0) || !(dt >= 0.0) || !std::isfinite(zeta) || !std::isfinite(dt))
     return fail(SIPG_EINVAL, "zeta and dt must be finite and >= 0");
@@ -557,7 +601,7 @@ int sipg_tau_div_f64(const sipg_mesh* m, const double* u, double zeta, double dt
 
 int sipg_apply_divdiv_f64(const sipg_mesh* m, const double* tau, const double* u, double* y, void* stream) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!tau || !u || !y) return fail(SIPG_EINVAL, "NULL vector");
   if (u == y) return fail(SIPG_EINVAL, "u and y must not overlap");
   if ((st = set_device(const_cast<sipg_mesh&>(*m)))) return st;
@@ -567,7 +611,7 @@ int sipg_apply_divdiv_f64(const sipg_mesh* m, const double* tau, const double* u
 int sipg_project_divdiv_f64(sipg_mesh* m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
                             void* stream, int* iters_out) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (!tau || !rhs || !x) return fail(SIPG_EINVAL, "NULL vector");
   if (rhs == x) return fail(SIPG_EINVAL, "rhs and x must not overlap");
   if (!(rtol >= 0.0) || maxit < 1) return fail(SIPG_EINVAL, "need rtol >= 0 and maxit >= 1");
@@ -608,7 +652,7 @@ int sipg_cg_noalloc_capacity(long long* bytes) {
 int sipg_adjoint_grad_nu(const sipg_mesh* mc, const double* nu_cell, const double* u, const double* lam,
                          double* grad, void* stream) {
   int st;
-  if ((st = check_mesh(mc))) return st;
+  if ((st = check_separable(mc))) return st;
   if (!nu_cell || !u || !lam || !grad) return fail(SIPG_EINVAL, "NULL argument");
   Mesh& m = const_cast<sipg_mesh&>(*mc);
   if ((st = set_device(m))) return st;
@@ -720,7 +764,7 @@ static int autotune_convective(sipg_mesh* m, int* best_out) {
 
 int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
   int st;
-  if ((st = check_mesh(m))) return st;
+  if ((st = check_separable(m))) return st;
   if (precision < 0 || precision > 2) return fail(SIPG_EINVAL, "precision must be 0, 1 or 2");
   char key[160];
   std::snprintf(key, sizeof(key), "k=%d prec=%d map=%d n=%dx%dx%d%s", m->k, precision, m->desc.map, m->desc.n[0],

@@ -412,12 +412,17 @@ __global__ void k_pupdate(const Scalars* __restrict__ sc, long long n, double* _
 // operator applied by several kernels
 __global__ void k_dot_sink(const int* __restrict__ skip, long long n, const double* __restrict__ x,
                            const double* __restrict__ y, double* __restrict__ part, unsigned* __restrict__ counter,
-                           double* __restrict__ totals) {
+                           double* __restrict__ totals, int sums) {
   if (*skip) return;
-  double xy = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+  double xy = 0.0, sy = 0.0, sx = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     xy += x[i] * y[i];
-  block_partial3(xy, 0.0, 0.0, part);
+    if (sums) {
+      sy += y[i];
+      sx += x[i];
+    }
+  }
+  block_partial3(xy, sy, sx, part);
   __shared__ int last;
   if (threadIdx.x == 0) {
     __threadfence();
@@ -426,21 +431,21 @@ __global__ void k_dot_sink(const int* __restrict__ skip, long long n, const doub
   __syncthreads();
   if (!last) return;
   __threadfence();
-  double s = 0.0;
-#pragma unroll 4
-  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(part + 3 * i);
-  double t[3];
-  __shared__ double sh[32];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  double s[3] = {0.0, 0.0, 0.0};
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x)
+    for (int k = 0; k < 3; ++k) s[k] += __ldcg(part + 3 * i + k);
+  __shared__ double sh[3][32];
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
+    if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = s[k];
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += sh[w];
-    t[0] = tot;
-    totals[0] = t[0];
-    totals[1] = 0.0;
-    totals[2] = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      double tot = 0.0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += sh[k][w];
+      totals[k] = tot;
+    }
     *counter = 0u;
   }
 }
@@ -674,7 +679,16 @@ struct Solver {
       st = launch_apply<double>(m, x, y, ncomp, cm, nu, nullptr, true, &skip_only, nullptr, s);
       if (!st) st = launch_viscous_t(m, x, y, nu, dots ? &w.sc->done : nullptr, s);
       if (!st && dots) {
-        k_dot_sink<<<kVecBlocks, kVecThreads, 0, s>>>(&w.sc->done, n, x, y, dots, &w.sc->cnt_apply, w.sc->tot);
+        k_dot_sink<<<kVecBlocks, kVecThreads, 0, s>>>(&w.sc->done, n, x, y, dots, &w.sc->cnt_apply, w.sc->tot, 0);
+        st = launched();
+        if (nb) *nb = kVecBlocks;
+      }
+    } else if (m.general()) {
+      // general map: the operator, then p.Ap (and the zero-mean sums)
+      st = launch_general(m, x, y, ncomp, cm, nu, true, dots ? &w.sc->done : nullptr, s);
+      if (!st && dots) {
+        k_dot_sink<<<kVecBlocks, kVecThreads, 0, s>>>(&w.sc->done, n, x, y, dots, &w.sc->cnt_apply, w.sc->tot,
+                                                      o.zero_mean ? 1 : 0);
         st = launched();
         if (nb) *nb = kVecBlocks;
       }

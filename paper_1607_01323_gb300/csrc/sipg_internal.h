@@ -98,6 +98,14 @@ struct Mesh {
   std::vector<double> hns;
   long long ns_off[3] = {0, 0, 0};
   double* dns64 = nullptr;
+  // general-metric store of SIPG_MAP_PERTURBED (general.cu): per cell G and
+  // det J w at the Gauss points, per face point w dA J^-1 n and w dA, tau_e
+  std::vector<double> hgen_head, htau_gen;
+  double* dgen_head = nullptr;
+  double* dgen_geo = nullptr;
+  double* dgen_face = nullptr;
+  double* dgen_tau = nullptr;
+  bool general() const { return desc.map == SIPG_MAP_PERTURBED; }
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
   int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
@@ -131,6 +139,14 @@ void lagrange_eval(const std::vector<double>& z, double x, std::vector<double>& 
 double map_coord(const sipg_mesh_desc& d, int dir, double s);
 // Rebuild host layer tables and upload them.
 int build_tables(Mesh& m);
+// The full map at global reference coordinates s (general.cu).
+void map_point(const sipg_mesh_desc& d, const double s[3], double x[3]);
+// The general-metric store of SIPG_MAP_PERTURBED (general.cu).
+int build_general(Mesh& m);
+// y = cm M x + nu A x on a general map, ncomp components (general.cu); the
+// kernel returns at once when *skip != 0.
+int launch_general(const Mesh& m, const double* x, double* y, int ncomp, double cm, double nu, bool stiffness,
+                   const int* skip, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels
 template <typename T>

@@ -376,6 +376,7 @@ int sipg_ns_create(const sipg_mesh_desc* desc, const sipg_ns_params* prm, sipg_n
   if (!desc || !prm || !out) return fail(SIPG_EINVAL, "NULL argument");
   *out = nullptr;
   if (prm->k < 2 || prm->k > 7) return fail(SIPG_EINVAL, "the stepper needs 2 <= k <= 7 (pressure wall data)");
+  if (desc->map == SIPG_MAP_PERTURBED) return fail(SIPG_EINVAL, "the stepper needs a separable map");
   if (!(prm->nu > 0.0) || !std::isfinite(prm->nu)) return fail(SIPG_EINVAL, "nu must be finite and > 0");
   if (!(prm->dt > 0.0) || !std::isfinite(prm->dt)) return fail(SIPG_EINVAL, "dt must be finite and > 0");
   if (prm->order < 1 || prm->order > 3) return fail(SIPG_EINVAL, "order must be 1, 2 or 3");

@@ -430,7 +430,7 @@ int build_tables(Mesh& m) {
     e = cudaMemcpy(m.dtabdf[dir], dd.data(), cnt * sizeof(dfl), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload geometry tables");
   }
-  return SIPG_OK;
+  return m.general() ? build_general(m) : SIPG_OK;
 }
 
 }  // namespace sipg

@@ -63,6 +63,11 @@ def test_host_only_entry_points(lib_path):
     d.bc_lo[0], d.bc_hi[0] = _lib.BC["periodic"], _lib.BC["dirichlet"]
     assert L.sipg_create_mesh(ctypes.byref(d), ctypes.byref(h)) == _lib.EINVAL
     assert b"periodic" in L.sipg_last_error()
+    for i in range(3):
+        d.bc_lo[i] = d.bc_hi[i] = _lib.BC["periodic"]
+    d.map, d.amplitude = _lib.MAP["perturbed"], -0.1
+    assert L.sipg_create_mesh(ctypes.byref(d), ctypes.byref(h)) == _lib.EINVAL
+    assert b"amplitude" in L.sipg_last_error()
     assert L.sipg_set_degree(None, 3) == _lib.EINVAL
     assert L.sipg_apply_laplace_f64(None, None, None, 1, None) == _lib.EINVAL
 
