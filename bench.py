@@ -529,7 +529,8 @@ def run_config(args):
     c5: adjoint gradient on the 32^3 k=3 channel with per-cell viscosity;
     v3c: divergence, gradient, tau_D and the div-div local projection of the
         pressure-projection step on the 32^3 k=4 channel;
-    ns: the dual-splitting time step (BDF3, V3c) on the 32^3 k=4 channel."""
+    ns: the dual-splitting time step (BDF3, V3c) on the 32^3 k=4 channel;
+    perturbed: the general-metric FP64 apply on a 32^3 perturbed box, k=4."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -671,6 +672,25 @@ def run_config(args):
             "pressure_iters": mean("pressure_iters"), "viscous_iters": mean("viscous_iters"),
             "projection_max_cell_iters": mean("projection_iters"), "nu": nu, "dt": dt, "order": 3,
             "rtol_pressure_viscous": 1e-6}
+    elif args.workload == "perturbed":
+        # the general-metric path: the 32^3 box with a smooth displacement,
+        # k = 4, FP64 Laplace apply with the metric stored per quadrature point
+        n_p = (args.cells,) * 3 if args.cells else (32, 32, 32)
+        kp = args.k if args.k else 4
+        m = Mesh(n_p, (0.0, -1.0, 0.0), (2 * math.pi, 1.0, math.pi), ("periodic", "dirichlet", "periodic"),
+                 ("periodic", "dirichlet", "periodic"), mapping="perturbed", k=kp, amplitude=0.05,
+                 seed=0x1234_5678_9ABC)
+        N = m.n_dofs
+        x = torch.tensor(inputs.uniform(0, "x", N), device="cuda")
+        y = torch.empty_like(x)
+        t, _ = _timed(lambda: [apply_laplace_f64(m, x, y) for _ in range(10)], reps=5)
+        t /= 10
+        p3 = (kp + 1) ** 3
+        geo_bytes = 7 * 8 + 6 * 4 * 8 * (kp + 1) ** 2 / p3  # per DoF: cell metric + face data
+        out["apply_general_f64"] = {"mesh": "%dx%dx%d perturbed box, k=%d" % (tuple(n_p) + (kp,)), "dofs": N,
+                                    "ms": 1e3 * t, "dofs_per_s": N / t,
+                                    "algorithmic_bytes_per_dof": 16 + geo_bytes,
+                                    "achieved_gbs": N * (16 + geo_bytes) / t / 1e9}
     elif args.workload == "v3c":
         # the pressure-projection neighbours of the Poisson solve (variant V3c)
         # on the 32^3 k=4 channel: divergence rhs, pressure gradient, tau_D
@@ -720,7 +740,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--f64", default="double_float", choices=["native", "double_float"],
                     help="arithmetic of the FP64 operator (double_float: FP32 pairs on the FP32 pipes)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "v3c", "ns"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "v3c", "ns", "perturbed"],
                     help="c2 (default) is the bench step; c1, c3-c5, v3c, ns print timings of other workloads")
     args = ap.parse_args()
     if args.mode == "apply":

@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
   __shared__ double su[P3], A1[P3], B1[P3], AA[P3], AB[P3], BA[P3], W[P3];
   __shared__ double sS[P2], sD[P2], sd0[P], sd1[P];
   __shared__ double fv[8][P2];
+  __shared__ double ih[6][P2];  // face intermediates
   const int e = blockIdx.x, comp = blockIdx.y;
   const int nt = blockDim.x, tid = threadIdx.x;
   const long long N = (long long)a.g.ncell * P3;
@@ -406,28 +407,41 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
         }
       }
       __syncthreads();
+      // to the face points in two 1D stages: along t1 (S for all four plane
+      // arrays, D for the two value planes), then along t2
+      for (int l = tid; l < 6 * P; l += nt) {
+        const int k = l / P, cc = l % P;  // k < 4: S of plane k; k = 4, 5: D of planes 0, 2
+        const double* src = fv[k < 4 ? k : (k == 4 ? 0 : 2)] + cc * P;
+        const double* M = k < 4 ? sS : sD;
+        if (k < 4 && kind != 0 && k >= 2) continue;
+        if (k == 5 && kind != 0) continue;
+        for (int q1 = 0; q1 < P; ++q1) {
+          double t = 0.0;
+          for (int b = 0; b < P; ++b) t = fma(M[q1 * P + b], src[b], t);
+          ih[k][cc * P + q1] = t;
+        }
+      }
+      __syncthreads();
       // flux at the face points
       const double* Fo = a.face + ((long long)e * 6 + f) * 4 * P2;
       const double* Fn = kind == 0 ? a.face + ((long long)nb * 6 + (2 * d + 1 - side)) * 4 * P2 : nullptr;
       const double tau_f = kind == 0 ? fmax(tau_e, a.tau[nb]) : tau_e;
       for (int q = tid; q < P2; q += nt) {
         const int q1 = q % P, q2 = q / P;
-        double val[4] = {0.0, 0.0, 0.0, 0.0}, d1v[4] = {0.0, 0.0, 0.0, 0.0}, d2v[4] = {0.0, 0.0, 0.0, 0.0};
+        // val: u, d_d u of both sides; d1: t1-derivative; d2: t2-derivative
+        double val[4] = {0.0, 0.0, 0.0, 0.0}, d1v[2] = {0.0, 0.0}, d2v[2] = {0.0, 0.0};
         const int nv = kind == 0 ? 4 : 2;
-        for (int cc = 0; cc < P; ++cc)
-          for (int b = 0; b < P; ++b) {
-            const double ws = sS[q1 * P + b] * sS[q2 * P + cc];
-            const double wd1 = sD[q1 * P + b] * sS[q2 * P + cc];
-            const double wd2 = sS[q1 * P + b] * sD[q2 * P + cc];
-            const int j = cc * P + b;
-            for (int k = 0; k < nv; ++k) {
-              val[k] = fma(ws, fv[k][j], val[k]);
-              if (k == 0 || k == 2) {
-                d1v[k] = fma(wd1, fv[k][j], d1v[k]);
-                d2v[k] = fma(wd2, fv[k][j], d2v[k]);
-              }
-            }
+        for (int cc = 0; cc < P; ++cc) {
+          const double ws = sS[q2 * P + cc], wd = sD[q2 * P + cc];
+          const int j = cc * P + q1;
+          for (int k = 0; k < nv; ++k) val[k] = fma(ws, ih[k][j], val[k]);
+          d1v[0] = fma(ws, ih[4][j], d1v[0]);
+          d2v[0] = fma(wd, ih[0][j], d2v[0]);
+          if (kind == 0) {
+            d1v[1] = fma(ws, ih[5][j], d1v[1]);
+            d2v[1] = fma(wd, ih[2][j], d2v[1]);
           }
+        }
         // reference gradients (x, y, z order) and d_n u w dA = grad . g
         double go[3], gn[3];
         go[d] = val[1];
@@ -438,8 +452,8 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
         double rv, rg;
         if (kind == 0) {
           gn[d] = val[3];
-          gn[t1] = d1v[2];
-          gn[t2] = d2v[2];
+          gn[t1] = d1v[1];
+          gn[t2] = d2v[1];
           // the neighbour's g carries its own outward normal, -n
           const double dn_nb = gn[0] * Fn[0 * P2 + q] + gn[1] * Fn[1 * P2 + q] + gn[2] * Fn[2 * P2 + q];
           const double jump = val[0] - val[2];
@@ -455,20 +469,34 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
         fv[7][q] = a.nu * rg * Fo[t2 * P2 + q];
       }
       __syncthreads();
-      // test functions: values and tangential derivatives on the end plane,
-      // the normal derivative along the lines through it
+      // test functions in two 1D stages: along t2 (q2 -> cc), then along t1
+      // (q1 -> b); values and tangential derivatives land on the end plane,
+      // the normal derivative on the lines through it
+      for (int l = tid; l < P2; l += nt) {
+        const int q1 = l % P, cc = l / P;
+        double tv = 0.0, tn = 0.0, tt1 = 0.0, tt2 = 0.0;
+        for (int q2 = 0; q2 < P; ++q2) {
+          const int q = q2 * P + q1;
+          const double ws = sS[q2 * P + cc];
+          tv = fma(ws, fv[4][q], tv);
+          tn = fma(ws, fv[5][q], tn);
+          tt1 = fma(ws, fv[6][q], tt1);
+          tt2 = fma(sD[q2 * P + cc], fv[7][q], tt2);
+        }
+        ih[0][cc * P + q1] = tv + tt2;
+        ih[1][cc * P + q1] = tn;
+        ih[2][cc * P + q1] = tt1;
+      }
+      __syncthreads();
       for (int j = tid; j < P2; j += nt) {
         const int b = j % P, cc = j / P, tr = b * s1 + cc * s2;
         double pv = 0.0, pn = 0.0;
-        for (int q2 = 0; q2 < P; ++q2)
-          for (int q1 = 0; q1 < P; ++q1) {
-            const int q = q2 * P + q1;
-            const double ws = sS[q1 * P + b] * sS[q2 * P + cc];
-            pv = fma(ws, fv[4][q], pv);
-            pv = fma(sD[q1 * P + b] * sS[q2 * P + cc], fv[6][q], pv);
-            pv = fma(sS[q1 * P + b] * sD[q2 * P + cc], fv[7][q], pv);
-            pn = fma(ws, fv[5][q], pn);
-          }
+        for (int q1 = 0; q1 < P; ++q1) {
+          const int t = cc * P + q1;
+          pv = fma(sS[q1 * P + b], ih[0][t], pv);
+          pv = fma(sD[q1 * P + b], ih[2][t], pv);
+          pn = fma(sS[q1 * P + b], ih[1][t], pn);
+        }
         W[end * sd + tr] += pv;
         for (int i = 0; i < P; ++i) W[i * sd + tr] = fma(dend[i], pn, W[i * sd + tr]);
       }
