@@ -95,9 +95,10 @@ typedef enum {
  *   coordinate in [0,1]^3, c_i = 2 f_i / 65535 - 1 with f_i the 16-bit field
  *   i of seed.
  * Its geometry is stored per quadrature point (56 B per DoF plus face data);
- * it supports the FP64 Laplace / Helmholtz / mass applies with a constant
- * viscosity and sipg_cg_solve with SIPG_PC_NONE; the other entry points need
- * a separable map and return SIPG_EINVAL. */
+ * it supports the FP64 Laplace / Helmholtz / mass applies and the diagonal
+ * with a constant viscosity, and sipg_cg_solve with SIPG_PC_NONE or
+ * SIPG_PC_JACOBI; the other entry points need a separable map and return
+ * SIPG_EINVAL. */
 typedef struct {
   int n[3];          /* cells per direction, each >= 1                         */
   double lo[3];      /* box corner                                             */

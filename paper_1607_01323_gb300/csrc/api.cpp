@@ -395,7 +395,7 @@ int sipg_apply_inverse_mass_f64(const sipg_mesh* mc, const double* x, double* y,
 int sipg_diagonal_f64(const sipg_mesh* mc, int op, double cm, double nu, const double* nu_cell, double* diag,
                       void* stream) {
   int st;
-  if ((st = check_separable(mc))) return st;
+  if ((st = check_mesh(mc))) return st;
   if (!diag) return fail(SIPG_EINVAL, "diag is NULL");
   if (op != SIPG_OP_LAPLACE && op != SIPG_OP_HELMHOLTZ) return fail(SIPG_EINVAL, "unknown operator");
   Mesh& m = const_cast<sipg_mesh&>(*mc);
@@ -449,9 +449,10 @@ int sipg_cg_solve(sipg_mesh* m, const sipg_cg_opts* o, const double* b, double* 
     if (o->zero_mean) return fail(SIPG_EINVAL, "zero_mean applies to the Laplace operator only");
   }
   if (o->precond < SIPG_PC_NONE || o->precond > SIPG_PC_GMG_F32) return fail(SIPG_EINVAL, "unknown preconditioner");
-  if (m->general() && (o->op == SIPG_OP_VISCOUS || o->precond != SIPG_PC_NONE || o->nu_cell))
+  if (m->general() && (o->op == SIPG_OP_VISCOUS || (o->precond != SIPG_PC_NONE && o->precond != SIPG_PC_JACOBI) ||
+                       o->nu_cell))
     return fail(SIPG_EINVAL, "on a perturbed mesh CG supports the Laplace / Helmholtz operator with a constant nu "
-                             "and SIPG_PC_NONE");
+                             "and SIPG_PC_NONE or SIPG_PC_JACOBI");
   if (o->precond == SIPG_PC_GMG_F32) {
     if (o->op != SIPG_OP_LAPLACE) return fail(SIPG_EINVAL, "the multigrid preconditioner supports the Laplace operator");
     if (ncomp != 1) return fail(SIPG_EINVAL, "the multigrid preconditioner supports one component");

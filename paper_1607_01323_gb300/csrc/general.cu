@@ -507,6 +507,100 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
   for (int i = tid; i < P3; i += nt) y[(long long)e * P3 + i] = W[i];
 }
 
+// diag(A)_i = a(phi_i, phi_i) on a general map: the cell term summed over the
+// Gauss points, and per face the flux of phi_i tested with phi_i, with phi_i
+// also as the neighbour's trace when a periodic direction has one cell (the
+// cell is its own neighbour).  One thread per node.
+template <int P>
+__global__ void __launch_bounds__(kGenThreads) general_diag_kernel(GenArgs a) {
+  constexpr int P2 = P * P, P3 = P2 * P;
+  __shared__ double sS[P2], sD[P2], sd0[P], sd1[P];
+  const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < P2; i += nt) {
+    sS[i] = a.head[i];
+    sD[i] = a.head[P2 + i];
+  }
+  for (int i = tid; i < P; i += nt) {
+    sd0[i] = a.head[2 * P2 + i];
+    sd1[i] = a.head[2 * P2 + P + i];
+  }
+  __syncthreads();
+  const double* G = a.geo + (long long)e * 7 * P3;
+  const int id[3] = {e % a.g.n[0], (e / a.g.n[0]) % a.g.n[1], e / (a.g.n[0] * a.g.n[1])};
+  const double tau_e = a.tau[e];
+  for (int node = tid; node < P3; node += nt) {
+    const int ia[3] = {node % P, (node / P) % P, node / P2};
+    double acc = 0.0;
+    for (int qc = 0; qc < P; ++qc)
+      for (int qb = 0; qb < P; ++qb)
+        for (int qa = 0; qa < P; ++qa) {
+          const int pt = (qc * P + qb) * P + qa;
+          const double sx = sS[qa * P + ia[0]], sy = sS[qb * P + ia[1]], sz = sS[qc * P + ia[2]];
+          const double gx = sD[qa * P + ia[0]] * sy * sz, gy = sx * sD[qb * P + ia[1]] * sz,
+                       gz = sx * sy * sD[qc * P + ia[2]];
+          double v = 0.0;
+          if (a.stiffness)
+            v = a.nu * (G[0 * P3 + pt] * gx * gx + G[3 * P3 + pt] * gy * gy + G[5 * P3 + pt] * gz * gz +
+                        2.0 * (G[1 * P3 + pt] * gx * gy + G[2 * P3 + pt] * gx * gz + G[4 * P3 + pt] * gy * gz));
+          const double ph = sx * sy * sz;
+          acc += v + a.cm * G[6 * P3 + pt] * ph * ph;
+        }
+    if (a.stiffness) {
+      for (int f = 0; f < 6; ++f) {
+        const int d = f >> 1, side = f & 1;
+        int nb, kind, jl;
+        face_neighbor(a.g, d, side, d == 0 ? id[0] : (d == 1 ? id[1] : id[2]), e, nb, kind, jl);
+        if (kind == SIPG_BC_NEUMANN) continue;
+        const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+        const int end = side ? P - 1 : 0, nend = P - 1 - end;
+        const double* dend = side ? sd1 : sd0;
+        const double* dnb = side ? sd0 : sd1;
+        const int ad = d == 0 ? ia[0] : (d == 1 ? ia[1] : ia[2]);
+        const int b = t1 == 0 ? ia[0] : ia[1], cc = t2 == 2 ? ia[2] : ia[1];
+        const bool self = kind == 0 && nb == e;  // one cell along a periodic direction
+        const double* Fo = a.face + ((long long)e * 6 + f) * 4 * P2;
+        const double* Fn = kind == 0 ? a.face + ((long long)nb * 6 + (2 * d + 1 - side)) * 4 * P2 : nullptr;
+        const double tau_f = kind == 0 ? fmax(tau_e, a.tau[nb]) : tau_e;
+        const double own = ad == end ? 1.0 : 0.0, oth = (self && ad == nend) ? 1.0 : 0.0;
+        for (int q2 = 0; q2 < P; ++q2)
+          for (int q1 = 0; q1 < P; ++q1) {
+            const int q = q2 * P + q1;
+            const double s1 = sS[q1 * P + b], s2 = sS[q2 * P + cc];
+            const double t1v = sD[q1 * P + b] * s2, t2v = s1 * sD[q2 * P + cc];
+            // phi on the own face and its reference gradient there
+            double go[3];
+            go[d] = dend[ad] * s1 * s2;
+            go[t1] = own * t1v;
+            go[t2] = own * t2v;
+            const double um = own * s1 * s2;
+            const double gdot = go[0] * Fo[0 * P2 + q] + go[1] * Fo[1 * P2 + q] + go[2] * Fo[2 * P2 + q];
+            const double wda = Fo[3 * P2 + q];
+            double rv, rg;
+            if (kind == 0) {
+              double gn[3] = {0.0, 0.0, 0.0};
+              double up = 0.0, dnn = 0.0;
+              if (self) {  // phi as the neighbour's trace on the opposite face
+                gn[d] = dnb[ad] * s1 * s2;
+                gn[t1] = oth * t1v;
+                gn[t2] = oth * t2v;
+                up = oth * s1 * s2;
+                dnn = gn[0] * Fn[0 * P2 + q] + gn[1] * Fn[1 * P2 + q] + gn[2] * Fn[2 * P2 + q];
+              }
+              const double jump = um - up;
+              rv = tau_f * wda * jump - 0.5 * (gdot - dnn);
+              rg = -0.5 * jump;
+            } else {
+              rv = 2.0 * tau_e * wda * um - gdot;
+              rg = -um;
+            }
+            acc += a.nu * (rv * um + rg * gdot);
+          }
+      }
+    }
+    a.y[(long long)e * P3 + node] = acc;
+  }
+}
+
 }  // namespace
 
 int launch_general(const Mesh& m, const double* x, double* y, int ncomp, double cm, double nu, bool stiffness,
@@ -541,6 +635,40 @@ int launch_general(const Mesh& m, const double* x, double* y, int ncomp, double 
   const_cast<Mesh&>(m).launches++;
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "general operator launch");
+}
+
+}  // namespace sipg
+
+namespace sipg {
+
+int launch_general_diagonal(const Mesh& m, bool stiffness, double cm, double nu, double* diag, cudaStream_t s) {
+  GenArgs a{};
+  a.g = make_geo<double>(m);
+  a.head = m.dgen_head;
+  a.geo = m.dgen_geo;
+  a.face = m.dgen_face;
+  a.tau = m.dgen_tau;
+  a.y = diag;
+  a.cm = cm;
+  a.nu = nu;
+  a.stiffness = stiffness ? 1 : 0;
+  switch (m.p) {
+#define SIPG_GEN_CASE(P) \
+  case P:                \
+    general_diag_kernel<P><<<(unsigned)m.ncell, kGenThreads, 0, s>>>(a); break;
+    SIPG_GEN_CASE(2)
+    SIPG_GEN_CASE(3)
+    SIPG_GEN_CASE(4)
+    SIPG_GEN_CASE(5)
+    SIPG_GEN_CASE(6)
+    SIPG_GEN_CASE(7)
+    SIPG_GEN_CASE(8)
+#undef SIPG_GEN_CASE
+    default: return fail(SIPG_EINVAL, "unsupported degree");
+  }
+  const_cast<Mesh&>(m).launches++;
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "general diagonal launch");
 }
 
 }  // namespace sipg

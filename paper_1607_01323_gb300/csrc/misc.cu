@@ -67,6 +67,10 @@ int launch_inverse_mass(const Mesh& m, const double* x, double* y, int ncomp, do
 
 int launch_diagonal(const Mesh& m, bool stiffness, double cm, double nu, const double* nu_cell, double* diag,
                     cudaStream_t s) {
+  if (m.general()) {
+    if (nu_cell) return fail(SIPG_EINVAL, "a perturbed mesh supports a constant viscosity only");
+    return launch_general_diagonal(m, stiffness, cm, nu, diag, s);
+  }
   SIPG_DISPATCH_P(launch_diagonal_p, m, stiffness, cm, nu, nu_cell, diag, s)
 }
 

@@ -147,6 +147,8 @@ int build_general(Mesh& m);
 // kernel returns at once when *skip != 0.
 int launch_general(const Mesh& m, const double* x, double* y, int ncomp, double cm, double nu, bool stiffness,
                    const int* skip, cudaStream_t s);
+// diag(cm M + nu A) on a general map (general.cu).
+int launch_general_diagonal(const Mesh& m, bool stiffness, double cm, double nu, double* diag, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels
 template <typename T>

@@ -3,7 +3,8 @@ smooth displacement, metric stored per quadrature point) against the oracle's
 dense-quadrature SIPG matrix: Laplace, Helmholtz and mass applies within
 1e-12 of ||A||_inf ||x||_inf, node coordinates and penalties, CG solves, and
 at a size the oracle cannot assemble, symmetry and the constant null space;
-entry points that need a separable map reject the mesh."""
+the diagonal and Jacobi-preconditioned CG; entry points that need a separable
+map reject the mesh."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -63,6 +64,13 @@ def test_perturbed_apply_parity(name, c, k):
     Mx = op.mass_apply(x)
     ym = apply_mass_f64(m, _cuda(x)).cpu().numpy()
     assert np.abs(ym - Mx).max() <= 1e-13 * np.abs(Mx).max()
+    # the diagonal (Jacobi), including self-coupling when a periodic
+    # direction has one cell
+    from paper_1607_01323_gb300 import diagonal_f64
+    dA = diagonal_f64(m).cpu().numpy()
+    assert np.abs(dA - A.diagonal()).max() <= 1e-12 * np.abs(A.diagonal()).max()
+    dH = diagonal_f64(m, op="helmholtz", mass_coef=1500.0, nu=1 / 180).cpu().numpy()
+    assert np.abs(dH - H.diagonal()).max() <= 1e-12 * np.abs(H.diagonal()).max()
 
 
 def test_perturbed_cg_solves():
@@ -75,6 +83,9 @@ def test_perturbed_cg_solves():
     assert res.converged
     x_ref = spla.spsolve(op.assemble().tocsc(), b)
     assert np.abs(x.cpu().numpy() - x_ref).max() <= 1e-9 * np.abs(x_ref).max()
+    xj, rj = cg_solve(m, _cuda(b), precond="jacobi", rtol=1e-12)
+    assert rj.converged and rj.iters <= res.iters + 2
+    assert np.abs(xj.cpu().numpy() - x_ref).max() <= 1e-9 * np.abs(x_ref).max()
     # singular periodic problem: zero-mean right-hand side and solve
     cp = pert((2, 2, 2))
     mp = gpu_mesh(cp, 2)
@@ -102,8 +113,7 @@ def test_perturbed_properties_at_size():
 
 
 def test_perturbed_rejections():
-    from paper_1607_01323_gb300 import (SipgError, apply_inverse_mass_f64, apply_laplace_f32, cg_solve,
-                                        diagonal_f64)
+    from paper_1607_01323_gb300 import SipgError, apply_inverse_mass_f64, apply_laplace_f32, cg_solve
     c = pert((2, 2, 2), ("dirichlet",) * 3, ("dirichlet",) * 3)
     m = gpu_mesh(c, 2)
     x = _cuda(uniform(m.n_dofs, "x"))
@@ -112,6 +122,6 @@ def test_perturbed_rejections():
     with pytest.raises(SipgError):
         apply_laplace_f32(m, x.float())
     with pytest.raises(SipgError):
-        diagonal_f64(m)
+        cg_solve(m, x, precond="invmass")
     with pytest.raises(SipgError):
-        cg_solve(m, x, precond="jacobi")
+        cg_solve(m, x, precond="gmg_f32")
