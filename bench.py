@@ -680,6 +680,7 @@ def run_config(args):
         m = Mesh(n_p, (0.0, -1.0, 0.0), (2 * math.pi, 1.0, math.pi), ("periodic", "dirichlet", "periodic"),
                  ("periodic", "dirichlet", "periodic"), mapping="perturbed", k=kp, amplitude=0.05,
                  seed=0x1234_5678_9ABC)
+        m.set_f64_arithmetic(args.f64)
         N = m.n_dofs
         x = torch.tensor(inputs.uniform(0, "x", N), device="cuda")
         y = torch.empty_like(x)

@@ -246,35 +246,37 @@ __host__ __device__ constexpr int gstride(int dir) {
   return dir == 0 ? 1 : (dir == 1 ? P : P * P);
 }
 
-template <int P>
-__global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
+template <typename T, int P>
+__global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a) {
   constexpr int P2 = P * P, P3 = P2 * P;
   if (a.skip && *a.skip) return;
-  __shared__ double su[P3], A1[P3], B1[P3], AA[P3], AB[P3], BA[P3], W[P3];
-  __shared__ double sS[P2], sD[P2], sd0[P], sd1[P];
-  __shared__ double fv[8][P2];
-  __shared__ double ih[6][P2];  // face intermediates
+  __shared__ T su[P3], A1[P3], B1[P3], AA[P3], AB[P3], BA[P3], W[P3];
+  __shared__ T sS[P2], sD[P2], sd0[P], sd1[P];
+  __shared__ T fv[8][P2];
+  __shared__ T ih[6][P2];  // face intermediates
   const int e = blockIdx.x, comp = blockIdx.y;
   const int nt = blockDim.x, tid = threadIdx.x;
   const long long N = (long long)a.g.ncell * P3;
   const double* x = a.x + comp * N;
-  for (int i = tid; i < P3; i += nt) su[i] = x[(long long)e * P3 + i];
+  for (int i = tid; i < P3; i += nt) su[i] = cvt_in<T, double>(x[(long long)e * P3 + i]);
   for (int i = tid; i < P2; i += nt) {
-    sS[i] = a.head[i];
-    sD[i] = a.head[P2 + i];
+    sS[i] = cvt_in<T, double>(a.head[i]);
+    sD[i] = cvt_in<T, double>(a.head[P2 + i]);
   }
   for (int i = tid; i < P; i += nt) {
-    sd0[i] = a.head[2 * P2 + i];
-    sd1[i] = a.head[2 * P2 + P + i];
+    sd0[i] = cvt_in<T, double>(a.head[2 * P2 + i]);
+    sd1[i] = cvt_in<T, double>(a.head[2 * P2 + P + i]);
   }
   __syncthreads();
+  const T cnu = cvt_in<T, double>(a.stiffness ? a.nu : 0.0), ccm = cvt_in<T, double>(a.cm);
+  const T fnu = cvt_in<T, double>(a.nu);
   const double* G = a.geo + (long long)e * 7 * P3;
   // x: A1 = S u, B1 = D u
   for (int l = tid; l < P2; l += nt) {
-    double v[P];
+    T v[P];
     for (int i = 0; i < P; ++i) v[i] = su[l * P + i];
     for (int q = 0; q < P; ++q) {
-      double s = 0.0, t = 0.0;
+      T s = T(0), t = T(0);
       for (int i = 0; i < P; ++i) {
         s = fma(sS[q * P + i], v[i], s);
         t = fma(sD[q * P + i], v[i], t);
@@ -287,13 +289,13 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
   // y: AA = S A1, AB = D A1, BA = S B1
   for (int l = tid; l < P2; l += nt) {
     const int qx = l % P, z = l / P, base = z * P2 + qx;
-    double va[P], vb[P];
+    T va[P], vb[P];
     for (int i = 0; i < P; ++i) {
       va[i] = A1[base + i * P];
       vb[i] = B1[base + i * P];
     }
     for (int q = 0; q < P; ++q) {
-      double s = 0.0, t = 0.0, r = 0.0;
+      T s = T(0), t = T(0), r = T(0);
       for (int i = 0; i < P; ++i) {
         s = fma(sS[q * P + i], va[i], s);
         t = fma(sD[q * P + i], va[i], t);
@@ -307,15 +309,15 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
   __syncthreads();
   // z: gradients and value at the points, the metric, the transposed z sweep
   for (int l = tid; l < P2; l += nt) {
-    double vaa[P], vab[P], vba[P];
+    T vaa[P], vab[P], vba[P];
     for (int i = 0; i < P; ++i) {
       vaa[i] = AA[l + i * P2];
       vab[i] = AB[l + i * P2];
       vba[i] = BA[l + i * P2];
     }
-    double fx[P], fy[P], fz[P], fm[P];
+    T fx[P], fy[P], fz[P], fm[P];
     for (int q = 0; q < P; ++q) {
-      double gx = 0.0, gy = 0.0, gz = 0.0, uq = 0.0;
+      T gx = T(0), gy = T(0), gz = T(0), uq = T(0);
       for (int i = 0; i < P; ++i) {
         gx = fma(sS[q * P + i], vba[i], gx);
         gy = fma(sS[q * P + i], vab[i], gy);
@@ -323,14 +325,16 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
         uq = fma(sS[q * P + i], vaa[i], uq);
       }
       const int pt = q * P2 + l;
-      const double nu = a.stiffness ? a.nu : 0.0;
-      fx[q] = nu * (G[0 * P3 + pt] * gx + G[1 * P3 + pt] * gy + G[2 * P3 + pt] * gz);
-      fy[q] = nu * (G[1 * P3 + pt] * gx + G[3 * P3 + pt] * gy + G[4 * P3 + pt] * gz);
-      fz[q] = nu * (G[2 * P3 + pt] * gx + G[4 * P3 + pt] * gy + G[5 * P3 + pt] * gz);
-      fm[q] = a.cm * G[6 * P3 + pt] * uq;
+      const T g0 = cvt_in<T, double>(G[0 * P3 + pt]), g1 = cvt_in<T, double>(G[1 * P3 + pt]);
+      const T g2 = cvt_in<T, double>(G[2 * P3 + pt]), g3 = cvt_in<T, double>(G[3 * P3 + pt]);
+      const T g4 = cvt_in<T, double>(G[4 * P3 + pt]), g5 = cvt_in<T, double>(G[5 * P3 + pt]);
+      fx[q] = cnu * fma(g0, gx, fma(g1, gy, g2 * gz));
+      fy[q] = cnu * fma(g1, gx, fma(g3, gy, g4 * gz));
+      fz[q] = cnu * fma(g2, gx, fma(g4, gy, g5 * gz));
+      fm[q] = ccm * cvt_in<T, double>(G[6 * P3 + pt]) * uq;
     }
     for (int i = 0; i < P; ++i) {
-      double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      T s1 = T(0), s2 = T(0), s3 = T(0);
       for (int q = 0; q < P; ++q) {
         s1 = fma(sS[q * P + i], fx[q], s1);
         s2 = fma(sS[q * P + i], fy[q], s2);
@@ -345,14 +349,14 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
   // transposed y: A1 = S^T AA + D^T AB, B1 = S^T BA
   for (int l = tid; l < P2; l += nt) {
     const int qx = l % P, z = l / P, base = z * P2 + qx;
-    double va[P], vb[P], vc[P];
+    T va[P], vb[P], vc[P];
     for (int i = 0; i < P; ++i) {
       va[i] = AA[base + i * P];
       vb[i] = AB[base + i * P];
       vc[i] = BA[base + i * P];
     }
     for (int i = 0; i < P; ++i) {
-      double s = 0.0, t = 0.0;
+      T s = T(0), t = T(0);
       for (int q = 0; q < P; ++q) {
         s = fma(sS[q * P + i], va[q], fma(sD[q * P + i], vb[q], s));
         t = fma(sS[q * P + i], vc[q], t);
@@ -364,13 +368,13 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
   __syncthreads();
   // transposed x: W = S^T A1 + D^T B1
   for (int l = tid; l < P2; l += nt) {
-    double va[P], vb[P];
+    T va[P], vb[P];
     for (int i = 0; i < P; ++i) {
       va[i] = A1[l * P + i];
       vb[i] = B1[l * P + i];
     }
     for (int i = 0; i < P; ++i) {
-      double s = 0.0;
+      T s = T(0);
       for (int q = 0; q < P; ++q) s = fma(sS[q * P + i], va[q], fma(sD[q * P + i], vb[q], s));
       W[l * P + i] = s;
     }
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
   // faces
   if (a.stiffness) {
     const int id[3] = {e % a.g.n[0], (e / a.g.n[0]) % a.g.n[1], e / (a.g.n[0] * a.g.n[1])};
-    const double tau_e = a.tau[e];
+    const double tau_e = a.tau[e];  // penalties stay FP64 (one conversion per face)
 #pragma unroll 1
     for (int f = 0; f < 6; ++f) {
       const int d = f >> 1, side = f & 1;
@@ -389,20 +393,20 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
       const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
       const int sd = gstride<P>(d), s1 = gstride<P>(t1), s2 = gstride<P>(t2);
       const int end = side ? P - 1 : 0, nend = P - 1 - end;
-      const double* dend = side ? sd1 : sd0;
-      const double* dnb = side ? sd0 : sd1;
+      const T* dend = side ? sd1 : sd0;
+      const T* dnb = side ? sd0 : sd1;
       // plane values and normal reference derivatives of both sides
       for (int j = tid; j < P2; j += nt) {
         const int b = j % P, cc = j / P, tr = b * s1 + cc * s2;
         fv[0][j] = su[end * sd + tr];
-        double nd = 0.0;
+        T nd = T(0);
         for (int i = 0; i < P; ++i) nd = fma(dend[i], su[i * sd + tr], nd);
         fv[1][j] = nd;
         if (kind == 0) {
           const double* xn = x + (long long)nb * P3;
-          fv[2][j] = xn[nend * sd + tr];
-          double nn = 0.0;
-          for (int i = 0; i < P; ++i) nn = fma(dnb[i], xn[i * sd + tr], nn);
+          fv[2][j] = cvt_in<T, double>(xn[nend * sd + tr]);
+          T nn = T(0);
+          for (int i = 0; i < P; ++i) nn = fma(dnb[i], cvt_in<T, double>(xn[i * sd + tr]), nn);
           fv[3][j] = nn;
         }
       }
@@ -411,12 +415,12 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
       // arrays, D for the two value planes), then along t2
       for (int l = tid; l < 6 * P; l += nt) {
         const int k = l / P, cc = l % P;  // k < 4: S of plane k; k = 4, 5: D of planes 0, 2
-        const double* src = fv[k < 4 ? k : (k == 4 ? 0 : 2)] + cc * P;
-        const double* M = k < 4 ? sS : sD;
+        const T* src = fv[k < 4 ? k : (k == 4 ? 0 : 2)] + cc * P;
+        const T* M = k < 4 ? sS : sD;
         if (k < 4 && kind != 0 && k >= 2) continue;
         if (k == 5 && kind != 0) continue;
         for (int q1 = 0; q1 < P; ++q1) {
-          double t = 0.0;
+          T t = T(0);
           for (int b = 0; b < P; ++b) t = fma(M[q1 * P + b], src[b], t);
           ih[k][cc * P + q1] = t;
         }
@@ -425,14 +429,14 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
       // flux at the face points
       const double* Fo = a.face + ((long long)e * 6 + f) * 4 * P2;
       const double* Fn = kind == 0 ? a.face + ((long long)nb * 6 + (2 * d + 1 - side)) * 4 * P2 : nullptr;
-      const double tau_f = kind == 0 ? fmax(tau_e, a.tau[nb]) : tau_e;
+      const T tau_f = cvt_in<T, double>(kind == 0 ? fmax(tau_e, a.tau[nb]) : tau_e), tau_o = cvt_in<T, double>(tau_e);
       for (int q = tid; q < P2; q += nt) {
         const int q1 = q % P, q2 = q / P;
         // val: u, d_d u of both sides; d1: t1-derivative; d2: t2-derivative
-        double val[4] = {0.0, 0.0, 0.0, 0.0}, d1v[2] = {0.0, 0.0}, d2v[2] = {0.0, 0.0};
+        T val[4] = {T(0), T(0), T(0), T(0)}, d1v[2] = {T(0), T(0)}, d2v[2] = {T(0), T(0)};
         const int nv = kind == 0 ? 4 : 2;
         for (int cc = 0; cc < P; ++cc) {
-          const double ws = sS[q2 * P + cc], wd = sD[q2 * P + cc];
+          const T ws = sS[q2 * P + cc], wd = sD[q2 * P + cc];
           const int j = cc * P + q1;
           for (int k = 0; k < nv; ++k) val[k] = fma(ws, ih[k][j], val[k]);
           d1v[0] = fma(ws, ih[4][j], d1v[0]);
@@ -443,30 +447,34 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
           }
         }
         // reference gradients (x, y, z order) and d_n u w dA = grad . g
-        double go[3], gn[3];
+        T go[3], gn[3];
         go[d] = val[1];
         go[t1] = d1v[0];
         go[t2] = d2v[0];
-        const double dn_own = go[0] * Fo[0 * P2 + q] + go[1] * Fo[1 * P2 + q] + go[2] * Fo[2 * P2 + q];
-        const double wda = Fo[3 * P2 + q];
-        double rv, rg;
+        const T fo0 = cvt_in<T, double>(Fo[0 * P2 + q]), fo1 = cvt_in<T, double>(Fo[1 * P2 + q]);
+        const T fo2 = cvt_in<T, double>(Fo[2 * P2 + q]);
+        const T dn_own = fma(go[0], fo0, fma(go[1], fo1, go[2] * fo2));
+        const T wda = cvt_in<T, double>(Fo[3 * P2 + q]);
+        T rv, rg;
         if (kind == 0) {
           gn[d] = val[3];
           gn[t1] = d1v[1];
           gn[t2] = d2v[1];
           // the neighbour's g carries its own outward normal, -n
-          const double dn_nb = gn[0] * Fn[0 * P2 + q] + gn[1] * Fn[1 * P2 + q] + gn[2] * Fn[2 * P2 + q];
-          const double jump = val[0] - val[2];
-          rv = tau_f * wda * jump - 0.5 * (dn_own - dn_nb);
-          rg = -0.5 * jump;
+          const T dn_nb = fma(gn[0], cvt_in<T, double>(Fn[0 * P2 + q]),
+                              fma(gn[1], cvt_in<T, double>(Fn[1 * P2 + q]), gn[2] * cvt_in<T, double>(Fn[2 * P2 + q])));
+          const T jump = val[0] - val[2];
+          rv = tau_f * wda * jump - T(0.5) * (dn_own - dn_nb);
+          rg = -(T(0.5) * jump);
         } else {  // Dirichlet
-          rv = 2.0 * tau_e * wda * val[0] - dn_own;
+          rv = T(2) * tau_o * wda * val[0] - dn_own;
           rg = -val[0];
         }
-        fv[4][q] = a.nu * rv;
-        fv[5][q] = a.nu * rg * Fo[d * P2 + q];
-        fv[6][q] = a.nu * rg * Fo[t1 * P2 + q];
-        fv[7][q] = a.nu * rg * Fo[t2 * P2 + q];
+        const T fo[3] = {fo0, fo1, fo2};
+        fv[4][q] = fnu * rv;
+        fv[5][q] = fnu * rg * fo[d];
+        fv[6][q] = fnu * rg * fo[t1];
+        fv[7][q] = fnu * rg * fo[t2];
       }
       __syncthreads();
       // test functions in two 1D stages: along t2 (q2 -> cc), then along t1
@@ -474,10 +482,10 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
       // the normal derivative on the lines through it
       for (int l = tid; l < P2; l += nt) {
         const int q1 = l % P, cc = l / P;
-        double tv = 0.0, tn = 0.0, tt1 = 0.0, tt2 = 0.0;
+        T tv = T(0), tn = T(0), tt1 = T(0), tt2 = T(0);
         for (int q2 = 0; q2 < P; ++q2) {
           const int q = q2 * P + q1;
-          const double ws = sS[q2 * P + cc];
+          const T ws = sS[q2 * P + cc];
           tv = fma(ws, fv[4][q], tv);
           tn = fma(ws, fv[5][q], tn);
           tt1 = fma(ws, fv[6][q], tt1);
@@ -490,21 +498,21 @@ __global__ void __launch_bounds__(kGenThreads) apply_general_kernel(GenArgs a) {
       __syncthreads();
       for (int j = tid; j < P2; j += nt) {
         const int b = j % P, cc = j / P, tr = b * s1 + cc * s2;
-        double pv = 0.0, pn = 0.0;
+        T pv = T(0), pn = T(0);
         for (int q1 = 0; q1 < P; ++q1) {
           const int t = cc * P + q1;
           pv = fma(sS[q1 * P + b], ih[0][t], pv);
           pv = fma(sD[q1 * P + b], ih[2][t], pv);
           pn = fma(sS[q1 * P + b], ih[1][t], pn);
         }
-        W[end * sd + tr] += pv;
+        W[end * sd + tr] = W[end * sd + tr] + pv;
         for (int i = 0; i < P; ++i) W[i * sd + tr] = fma(dend[i], pn, W[i * sd + tr]);
       }
       __syncthreads();
     }
   }
   double* y = a.y + comp * N;
-  for (int i = tid; i < P3; i += nt) y[(long long)e * P3 + i] = W[i];
+  for (int i = tid; i < P3; i += nt) y[(long long)e * P3 + i] = cvt_out<double, T>(W[i]);
 }
 
 // diag(A)_i = a(phi_i, phi_i) on a general map: the cell term summed over the
@@ -621,7 +629,11 @@ int launch_general(const Mesh& m, const double* x, double* y, int ncomp, double 
   switch (m.p) {
 #define SIPG_GEN_CASE(P) \
   case P:                \
-    apply_general_kernel<P><<<grid, kGenThreads, 0, s>>>(a); break;
+    if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT)             \
+      apply_general_kernel<dfl, P><<<grid, kGenThreads, 0, s>>>(a); \
+    else                                                  \
+      apply_general_kernel<double, P><<<grid, kGenThreads, 0, s>>>(a); \
+    break;
     SIPG_GEN_CASE(2)
     SIPG_GEN_CASE(3)
     SIPG_GEN_CASE(4)

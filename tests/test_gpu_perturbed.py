@@ -43,11 +43,13 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("arith", ["native", "double_float"])
 @pytest.mark.parametrize("name,c,k", CASES, ids=[x[0] for x in CASES])
-def test_perturbed_apply_parity(name, c, k):
+def test_perturbed_apply_parity(name, c, k, arith):
     from paper_1607_01323_gb300 import apply_helmholtz_f64, apply_laplace_f64, apply_mass_f64
     op = SIPG(oracle_spec(c), k)
     m = gpu_mesh(c, k)
+    m.set_f64_arithmetic(arith)
     assert np.abs(m.node_coordinates() - op.node_coordinates().reshape(-1, 3)).max() <= 1e-14
     assert np.allclose(m.penalty_values(), op.tau, rtol=1e-12, atol=0)
     x = uniform(m.n_dofs, "x", seed=31)
@@ -102,6 +104,7 @@ def test_perturbed_properties_at_size():
     """16^3 cells at k = 3 (262,144 DoF): v.Au = u.Av and A 1 = 0 (periodic)."""
     from paper_1607_01323_gb300 import apply_laplace_f64
     m = gpu_mesh(pert((16, 16, 16), amp=0.04), 3)
+    m.set_f64_arithmetic("double_float")
     u = _cuda(uniform(m.n_dofs, "u", seed=35))
     v = _cuda(uniform(m.n_dofs, "v", seed=36))
     Au, Av = apply_laplace_f64(m, u), apply_laplace_f64(m, v)
