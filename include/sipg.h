@@ -312,8 +312,10 @@ int sipg_tau_div_f64(const sipg_mesh* mesh, const double* u, double zeta, double
 int sipg_apply_divdiv_f64(const sipg_mesh* mesh, const double* tau, const double* u, double* y, void* stream);
 
 /* Solve (M + tau_e B) x = rhs on every cell independently (the local
- * projection of Eq. (div-div)) by CG preconditioned with the tensorial
- * inverse mass matrix, one thread block per cell; x holds the initial guess
+ * projection of Eq. (div-div)) by CG preconditioned with the inverse of the
+ * component-diagonal blocks, (M_d + tau_e K_d)^-1 along d and the 1D inverse
+ * mass along the other directions (exact tensor products; the tensorial
+ * M^-1 when tau_e = 0), one thread block per cell; x holds the initial guess
  * on entry.  A cell stops when ||r|| <= rtol ||rhs_e|| or after maxit
  * iterations.  Synchronous.  iters_out (HOST, may be NULL) receives the
  * largest iteration count over the cells.  Returns SIPG_MAXITER if a cell did

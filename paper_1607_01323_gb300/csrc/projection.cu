@@ -251,15 +251,53 @@ __device__ void divdiv_cell(const CellCtxT<T>& cc, T tau, const T* u, T* y, T* t
   }
 }
 
-// z = M^-1 r per component (tensorial inverse mass, Sec. 5)
+// z = P^-1 r per component with the block preconditioner of (M + tau B):
+// component d's diagonal block (M_d + tau K_d) (x) M (x) M is a tensor
+// product, so its inverse is Pk[d] = (M_d + tau K_d)^-1 along d and the 1D
+// inverse mass along the other two directions.
 template <int P, typename T>
-__device__ void invmass_cell(const CellCtxT<T>& cc, const T* r, T* z, T* t1, T* t2) {
+__device__ void blockprec_cell(const CellCtxT<T>& cc, const T* Pk, const T* r, T* z, T* t1, T* t2) {
   using O = LayerOff<P>;
-  constexpr int P3 = P * P * P;
-  const T* A[3] = {cc.L[0] + O::Mi, cc.L[1] + O::Mi, cc.L[2] + O::Mi};
-  const T* B[3] = {nullptr, nullptr, nullptr};
-  const T cB[3] = {T(0), T(0), T(0)};
-  for (int d = 0; d < 3; ++d) cell_chain<P>(cc, A, B, cB, r + d * P3, z + d * P3, t1, t2, 0, T(1));
+  constexpr int P2 = P * P, P3 = P * P * P;
+  for (int d = 0; d < 3; ++d) {
+    const T* A[3] = {cc.L[0] + O::Mi, cc.L[1] + O::Mi, cc.L[2] + O::Mi};
+    A[d] = Pk + d * P2;
+    const T* B[3] = {nullptr, nullptr, nullptr};
+    const T cB[3] = {T(0), T(0), T(0)};
+    cell_chain<P>(cc, A, B, cB, r + d * P3, z + d * P3, t1, t2, 0, T(1));
+  }
+}
+
+// Pk[d] = (M_d + tau K_d)^-1 for d < 3 (FP64 Gauss-Jordan of an SPD P x P
+// matrix, one thread per direction); the caller synchronises.
+template <int P, typename T>
+__device__ void blockprec_setup(const CellCtxT<T>& cc, double tau, T* Pk) {
+  using O = LayerOff<P>;
+  constexpr int P2 = P * P;
+  if (threadIdx.x < 3) {
+    const int d = threadIdx.x;
+    double a[P2], inv[P2];
+    for (int i = 0; i < P2; ++i) {
+      a[i] = cvt_out<double, T>(cc.L[d][O::M + i]) + tau * cvt_out<double, T>(cc.L[d][O::K + i]);
+      inv[i] = (i / P == i % P) ? 1.0 : 0.0;
+    }
+    for (int c = 0; c < P; ++c) {
+      const double piv = 1.0 / a[c * P + c];
+      for (int j = 0; j < P; ++j) {
+        a[c * P + j] *= piv;
+        inv[c * P + j] *= piv;
+      }
+      for (int r = 0; r < P; ++r) {
+        if (r == c) continue;
+        const double f = a[r * P + c];
+        for (int j = 0; j < P; ++j) {
+          a[r * P + j] -= f * a[c * P + j];
+          inv[r * P + j] -= f * inv[c * P + j];
+        }
+      }
+    }
+    for (int i = 0; i < P2; ++i) Pk[d * P2 + i] = cvt_in<T, double>(inv[i]);
+  }
 }
 
 // sum of v over the block (blockDim <= 1024), result broadcast to all threads
@@ -318,8 +356,9 @@ __global__ void divdiv_apply_kernel(Geo<double> g, const double* __restrict__ Cg
   for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x) y[(i / P3) * N + (long long)e * P3 + i % P3] = sy[i];
 }
 
-// Per-cell CG on (M + tau B) x = rhs with z = M^-1 r; x holds the initial
-// guess.  status[0] |= 1 if a cell stops at maxit, |= 2 on breakdown;
+// Per-cell CG on (M + tau B) x = rhs, preconditioned by the inverse of its
+// component-diagonal blocks (blockprec_cell; M^-1 when tau = 0); x holds the
+// initial guess.  status[0] |= 1 if a cell stops at maxit, |= 2 on breakdown;
 // status[1] = max iterations over the cells.  T = double or dfl: the vectors
 // and contractions in T, the dot products summed per thread in T and over the
 // block in FP64, the CG scalars in FP64.
@@ -338,7 +377,8 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
   T* t2 = t1 + P3;
   T* C = t2 + P3;
   T* Ct = C + P * P;
-  double* red = reinterpret_cast<double*>(Ct + P * P);  // 32
+  T* Pk = Ct + P * P;  // [3][P2] block preconditioner
+  double* red = reinterpret_cast<double*>(Pk + 3 * P * P);  // 32
   const int e = blockIdx.x;
   const long long N = (long long)g.ncell * P3;
   double bb = 0.0;
@@ -350,9 +390,10 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
     bb += b * b;
   }
   stage_c<P>(Cg, C, Ct);
+  const CellCtxT<T> cc = cell_ctx<P>(g, e, (const T*)C, (const T*)Ct);
+  blockprec_setup<P>(cc, tau[e], Pk);
   __syncthreads();
   bb = block_sum(bb, red);
-  const CellCtxT<T> cc = cell_ctx<P>(g, e, (const T*)C, (const T*)Ct);
   const T te = cvt_in<T, double>(tau[e]);
   // r = rhs - A x
   divdiv_cell<P>(cc, te, sx, sq, t1, t2);
@@ -363,7 +404,7 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
   }
   __syncthreads();
   double rr = block_sum(cvt_out<double, T>(acc), red);
-  invmass_cell<P>(cc, sr, sz, t1, t2);
+  blockprec_cell<P>(cc, Pk, sr, sz, t1, t2);
   acc = T(0);
   for (int i = threadIdx.x; i < V; i += blockDim.x) {
     sp[i] = sz[i];
@@ -393,7 +434,7 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
     }
     __syncthreads();
     rr = block_sum(cvt_out<double, T>(acc), red);
-    invmass_cell<P>(cc, sr, sz, t1, t2);
+    blockprec_cell<P>(cc, Pk, sr, sz, t1, t2);
     acc = T(0);
     for (int i = threadIdx.x; i < V; i += blockDim.x) acc = fma(sr[i], sz[i], acc);
     const double rzn = block_sum(cvt_out<double, T>(acc), red);
@@ -641,7 +682,7 @@ template <int P>
 int launch_divdiv_solve_p(const Mesh& m, const double* tau, const double* rhs, double* x, double rtol, int maxit,
                           int* status, cudaStream_t s) {
   constexpr int P3 = P * P * P;
-  const size_t smem = (size_t)(12 * P3 + 2 * P3 + 2 * P * P + 32) * sizeof(double);
+  const size_t smem = (size_t)(12 * P3 + 2 * P3 + 5 * P * P + 32) * sizeof(double);
   const bool df = m.f64_arith == SIPG_F64_DOUBLE_FLOAT;
   cudaError_t e;
   if (smem > 48 * 1024) {
