@@ -80,3 +80,43 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_stepper_parameters_rejected_on_host(lib_path):
+    """sipg_ns_create validates its parameters before any CUDA call."""
+    from paper_1607_01323_gb300 import _lib
+    L = _lib.lib()
+    prm = _lib.NsParams()
+    assert L.sipg_ns_default_params(ctypes.byref(prm)) == 0
+    assert prm.k == 3 and prm.order == 3 and prm.zeta == 1.0 and prm.pressure_precond == _lib.PC["jacobi"]
+    d = _lib.MeshDesc()
+    for i in range(3):
+        d.n[i], d.hi[i] = 2, 1.0
+        d.bc_lo[i] = d.bc_hi[i] = _lib.BC["periodic"]
+    d.bc_lo[1] = d.bc_hi[1] = _lib.BC["dirichlet"]
+    h = ctypes.c_void_p()
+
+    def rejected(**changes):
+        p = _lib.NsParams()
+        L.sipg_ns_default_params(ctypes.byref(p))
+        for k, v in changes.items():
+            setattr(p, k, v)
+        return L.sipg_ns_create(ctypes.byref(d), ctypes.byref(p), ctypes.byref(h)) == _lib.EINVAL
+
+    assert rejected(k=1)           # the pressure wall data need k >= 2
+    assert rejected(order=4)
+    assert rejected(nu=0.0)
+    assert rejected(dt=-1.0)
+    assert rejected(zeta=-1.0)
+    assert rejected(pressure_precond=_lib.PC["invmass"])
+    assert rejected(rtol_viscous=0.0)
+    assert rejected(maxit_projection=0)
+    d.bc_lo[1] = d.bc_hi[1] = _lib.BC["neumann"]  # outflow boundaries are not supported
+    assert rejected()
+    assert b"periodic sides and no-slip walls" in L.sipg_last_error()
+    d.bc_lo[1] = d.bc_hi[1] = _lib.BC["dirichlet"]
+    d.map, d.amplitude = _lib.MAP["perturbed"], 0.05
+    assert rejected()
+    assert b"separable" in L.sipg_last_error()
+    assert L.sipg_ns_step(None, None, None, None) == _lib.EINVAL
+    assert L.sipg_ns_set_velocity(None, 0, None, None) == _lib.EINVAL
