@@ -150,3 +150,37 @@ def test_stepper_errors():
     ns.set_velocity(u)
     st = ns.step()
     assert st["order"] == 1 and ns.velocity().abs().max().item() == 0.0
+
+
+def test_long_run_stability_and_divergence():
+    """Stability and divergence over 200 steps (the metrics the paper checks
+    for the splitting, Sec. 4): a noisy start on the 8^3 k = 3 tanh channel at
+    low Reynolds number (nu = 0.2, f = 2 nu) relaxes towards Poiseuille flow,
+    the perturbation energy decays, and the weak divergence D u stays small
+    relative to the velocity's own scale."""
+    from paper_1607_01323_gb300 import apply_divergence_f64, apply_mass_f64
+    c = channel((8, 8, 8))
+    nu, dt = 0.2, 0.01
+    ns = _ns(c, 3, nu=nu, dt=dt, order=3, zeta=1.0, pressure_precond="gmg_f32", rtol_pressure=1e-8,
+             rtol_viscous=1e-8, rtol_projection=1e-10)
+    X = ns.velocity_mesh.node_coordinates()
+    N = ns.n_dofs
+    up = np.concatenate([1 - X[:, 1] ** 2, 0 * X[:, 0], 0 * X[:, 0]])
+    u0 = _velocity(X, 7, amp=0.3)
+    ns.set_velocity(_cuda(u0))
+    m = ns.velocity_mesh
+
+    def energy(v):
+        d = _cuda(v - up)
+        return torch.dot(d, apply_mass_f64(m, d)).item()
+
+    e0 = energy(u0)
+    div0 = apply_divergence_f64(m, _cuda(u0)).abs().max().item()
+    for s in range(200):
+        st = ns.step((2 * nu, 0.0, 0.0))
+        assert st["pressure_iters"] <= 60 and st["viscous_iters"] <= 60
+    u = ns.velocity().cpu().numpy()
+    assert np.isfinite(u).all()
+    assert energy(u) <= 0.2 * e0  # the perturbation decays
+    div = apply_divergence_f64(m, _cuda(u)).abs().max().item()
+    assert div <= 0.05 * div0  # the projection keeps the velocity nearly solenoidal
