@@ -293,6 +293,15 @@ def run_ours(args):
     value, t_total = aggregate_replicas(sum(t_steps) / 1e3, n_applies * N, dist if world > 1 else None)
     ms_per_step = 1e3 * t_total / args.steps
 
+    # accuracy of the last solve: || u_h - I u ||_M against the nodal interpolant
+    # of the exact solution u = sin x cos(pi y/2) sin 2z (a diagnostic, outside
+    # the timed region)
+    import numpy as np
+    u_ex = torch.tensor(np.sin(X[:, 0]) * np.cos(math.pi * X[:, 1] / 2) * np.sin(2 * X[:, 2]), device="cuda")
+    err = x - u_ex
+    l2_err = math.sqrt(max(torch.dot(err, apply_mass_f64(m, err)).item(), 0.0))
+    l2_u = math.sqrt(torch.dot(u_ex, apply_mass_f64(m, u_ex)).item())
+
     # end to end through the public API: pinned host rhs -> device, solve, solution -> host
     hb = torch.empty(N, dtype=torch.float64, pin_memory=True)
     hb.copy_(b.cpu())
@@ -401,6 +410,8 @@ def run_ours(args):
                    "double_float: FP64 data in HBM, operator in FP32 pairs (~2^-46), CG vectors in FP64",
                    "parallelism": "replicas" if world > 1 else "single"},
         "time_to_solve_s": ms_per_step / 1e3,
+        "solution_error": {"l2_vs_nodal_interpolant": l2_err, "relative": l2_err / l2_u,
+                           "note": "|| u_h - I u ||_M of the manufactured solution after the timed solves"},
         "apply_f64": {"avg_ms": avg_apply_ms, "dofs_per_s": N / (avg_apply_ms / 1e3), "timed_launches": applies,
                       "hbm_frac": (bytes_apply / (avg_apply_ms / 1e3) / 1e9) / hbm if hbm else None},
         "apply_f32": {"avg_ms": f32_ms, "dofs_per_s": N / (f32_ms / 1e3),
@@ -409,6 +420,10 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved_tflops,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved_tflops / peak,
                      "traffic": traffic, "peak_source": peak_source, "flops_per_dof": flops_per_dof,
+                     "bound_dofs_per_s": min(hbm * 1e9 / 16.0 if hbm else float("inf"),
+                                             peak * 1e12 / flops_per_dof),
+                     "apply_frac_of_bound": (N / (avg_apply_ms / 1e3)) / min(
+                         hbm * 1e9 / 16.0 if hbm else float("inf"), peak * 1e12 / flops_per_dof),
                      "hbm": {"achieved_gbs": bytes_apply / (avg_apply_ms / 1e3) / 1e9, "peak_gbs": hbm,
                              "frac": (bytes_apply / (avg_apply_ms / 1e3) / 1e9) / hbm if hbm else None,
                              "bytes_per_dof": 16}},
