@@ -421,8 +421,10 @@ int sipg_ns_set_velocity(sipg_ns* ns, int level, const double* u, void* stream);
 
 /* Advance one step with the body force f (HOST, 3 doubles, or NULL = 0) at
  * t^(n+1).  Synchronous (the solves read convergence data).  stats (HOST) may
- * be NULL.  Returns SIPG_MAXITER if a solve stopped at its bound, the
- * solvers' statuses otherwise. */
+ * be NULL.  Returns SIPG_MAXITER if a solve stopped at its bound (the step is
+ * completed with the last iterates), the solvers' statuses otherwise.  After
+ * any other error the stepper's history is undefined: set the velocity
+ * levels again before the next step. */
 int sipg_ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stats);
 
 /* Copy the current velocity (3 * n_dofs) or pressure (n_dofs) to DEVICE
