@@ -423,8 +423,8 @@ int sipg_ns_set_velocity(sipg_ns* ns, int level, const double* u, void* stream);
  * t^(n+1).  Synchronous (the solves read convergence data).  stats (HOST) may
  * be NULL.  Returns SIPG_MAXITER if a solve stopped at its bound (the step is
  * completed with the last iterates), the solvers' statuses otherwise.  After
- * any other error the stepper's history is undefined: set the velocity
- * levels again before the next step. */
+ * any other error the stepper forgets its history (a slot may hold part of
+ * the new level): set the velocity levels again before the next step. */
 int sipg_ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stats);
 
 /* Copy the current velocity (3 * n_dofs) or pressure (n_dofs) to DEVICE

@@ -491,8 +491,20 @@ int sipg_ns_set_velocity(sipg_ns* ns, int level, const double* u, void* stream) 
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "set velocity");
 }
 
+static int ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stats);
+
 int sipg_ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stats) {
   if (!ns) return fail(SIPG_EINVAL, "stepper is NULL");
+  const int st = ns_step(ns, f, stream, stats);
+  if (st != SIPG_OK && st != SIPG_MAXITER && ns->nlev > 0) {
+    // a slot may already hold part of the new level: forget the history
+    ns->nlev = 0;
+    ns->npl = 0;
+  }
+  return st;
+}
+
+static int ns_step(sipg_ns* ns, const double* f, void* stream, sipg_ns_stats* stats) {
   if (ns->nlev < 1) return fail(SIPG_EINVAL, "set the velocity (level 0) before stepping");
   int st;
   if ((st = ns_device(*ns))) return st;
