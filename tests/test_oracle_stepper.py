@@ -148,3 +148,33 @@ def test_taylor_green_temporal_orders():
     assert math.log2(err[(2, 2)][0] / err[(2, 4)][0]) >= 1.6
     assert math.log2(err[(3, 2)][1] / err[(3, 4)][1]) >= 2.6
     assert err[(3, 4)][0] <= 2e-5 and err[(3, 4)][1] <= 1e-3
+
+
+def test_shear_wave_between_walls_temporal_orders():
+    """u = (cos(pi y / 2) exp(-nu pi^2 t / 4), 0, 0) between no-slip walls at
+    y = -1, 1 is an exact solution with constant pressure: the split step is
+    then the BDF-J scheme for the heat equation, of order J, walls included
+    (1 x 4 x 1 affine cells, k = 5, nu = 0.5, T = 1, older levels exact)."""
+    nu, T = 0.5, 1.0
+    spec = MeshSpec(1, 4, 1, lo=(0.0, -1.0, 0.0), hi=(1.0, 1.0, 1.0), bc_lo=(P_, D_, P_), bc_hi=(P_, D_, P_))
+    ds = DualSplitting(spec, 5, nu, 0.25, order=2, zeta=1.0)
+    X = ds.sipg.node_coordinates().reshape(-1, 3)
+    lam = nu * math.pi ** 2 / 4
+
+    def ue(t):
+        return np.concatenate([np.cos(math.pi * X[:, 1] / 2) * math.exp(-lam * t), 0 * X[:, 0], 0 * X[:, 0]])
+
+    err = {}
+    for J in (2, 3):
+        ds.order = J
+        for Nst in (4, 8):
+            dt = T / Nst
+            ds.reset(dt)
+            ds.set_history([ue(-i * dt) for i in range(J)])
+            for _ in range(Nst):
+                u, p, _ = ds.step()
+            err[(J, Nst)] = np.abs(u - ue(T)).max()
+            assert np.abs(p - p.mean()).max() <= 1e-8  # constant pressure
+    assert math.log2(err[(2, 4)] / err[(2, 8)]) >= 1.8
+    assert math.log2(err[(3, 4)] / err[(3, 8)]) >= 2.8
+    assert err[(3, 8)] <= 1e-3
