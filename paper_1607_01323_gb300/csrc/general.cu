@@ -14,7 +14,9 @@
 //   -(v, {{d_n u}}) - (d_n v, [u]/2) + tau [u] v        interior (and periodic),
 //   -(v, d_n u) - (d_n v, u) + 2 tau_e u v              Dirichlet,
 // nothing on Neumann faces, and the transposed contractions into the cell's
-// own outputs (no atomics).  FP64; one cell and component per block.
+// own outputs (no atomics).  FP64 data; the arithmetic in FP64 or in
+// double-float with the mesh's setting; one cell and component per block.
+// The diagonal (Jacobi) sums a(phi_i, phi_i) directly per node.
 #include <cmath>
 #include <vector>
 
