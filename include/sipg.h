@@ -224,23 +224,29 @@ int sipg_cg_solve(sipg_mesh* mesh, const sipg_cg_opts* opts, const double* b, do
  *
  * The caller still passes b and x (DEVICE, as for sipg_cg_solve).  The solver's
  * workspace (5 vectors, the diagonal, partial sums, the solver record) comes
- * from one file-scope __device__ array of 16 MiB inside libsipg: every GPU that
- * loads the library holds those 16 MiB until the process exits.  That bounds the
- * problem to about 348,000 unknowns (ncomp * n_dofs); larger problems are
- * rejected with SIPG_EINVAL and a message giving the bytes needed.  The
- * function calls no cudaMalloc, cudaFree or other allocating routine, creates
- * no stream, event or graph, and runs on `stream` directly; it is synchronous
- * like sipg_cg_solve.  Preconditioners: SIPG_PC_NONE, SIPG_PC_JACOBI,
+ * from one file-scope __device__ array of 16 MiB inside libsipg.  A GPU holds
+ * those 16 MiB from the moment the library's CG module is loaded on it until
+ * the process exits; with CUDA's lazy module loading (the default) that load
+ * can be the first call of this function, which then makes a driver-side
+ * reservation, so make one warm-up call outside any stream capture and any
+ * allocation-sensitive region.  The array bounds the problem to about 348,000
+ * unknowns (ncomp * n_dofs); larger problems are rejected with SIPG_EINVAL and
+ * a message giving the bytes needed.  The function calls no cudaMalloc,
+ * cudaFree or other allocating routine, creates no stream, event or graph,
+ * and runs on `stream` directly; it is synchronous like sipg_cg_solve.  In
+ * double-float arithmetic it uses the mesh's scale word, which
+ * sipg_create_mesh allocated.  Preconditioners: SIPG_PC_NONE, SIPG_PC_JACOBI,
  * SIPG_PC_INVMASS (SIPG_PC_CHEB_F32 needs FP32 buffers and is rejected);
- * use_graph is ignored and the mesh's profiling is not applied.
+ * use_graph is ignored, no per-apply timing is recorded, and the mesh's
+ * profiling setting is left as it is.
  *
- * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture on the device.  Every call shares the
- * array and it keeps the previous call's contents (the solver clears what must
- * start from zero), so calls that overlap on the GPU -- on two streams, two host
- * threads or two meshes at once -- race on the array and must be serialised by
- * the caller.  Returns the same statuses as sipg_cg_solve. */
+ * Every call looks up the array's device address (cudaGetSymbolAddress, with
+ * the mesh's device current), so the address stays right across a
+ * cudaDeviceReset.  Every call shares the array and it keeps the previous
+ * call's contents (the solver clears what must start from zero), so calls
+ * that overlap on the GPU -- on two streams, two host threads or two meshes at
+ * once -- race on the array and must be serialised by the caller.  Returns the
+ * same statuses as sipg_cg_solve. */
 int sipg_cg_solve_noalloc(sipg_mesh* mesh, const sipg_cg_opts* opts, const double* b, double* x, int ncomp,
                           void* stream, int* iters_out, double* relres_out);
 
@@ -467,8 +473,26 @@ int sipg_autotune(sipg_mesh* mesh, int precision, const char* cache_path);
  * pipes, which issue 64 times the FP64 rate on GB300; results stay within the
  * FP64 parity tolerance (1e-12 of ||A|| ||x||).  The same choice applies to
  * sipg_apply_inverse_mass_f64 (and the inverse-mass preconditioner), to the
- * per-cell-viscosity Helmholtz operator and to sipg_apply_mass_f64; the
- * diagonal and the adjoint-gradient kernels always use FP64. */
+ * per-cell-viscosity Helmholtz operator, to sipg_apply_mass_f64, to the
+ * general-map operator, the convective term, the viscous coupling and the
+ * local div-div projection; the diagonal and the adjoint-gradient kernels
+ * always use FP64.
+ *
+ * Range: every double-float call first reduces the largest exponent of the
+ * finite entries of its FP64 input (one extra pass over the input, or, inside
+ * CG, in the search-direction update) and evaluates input * 2^-s with
+ * max |input| 2^-s in [1/2, 1), scaling the results back by the exact power
+ * of two.  FP64 data anywhere in the FP64 range (subnormals included) keep
+ * their 48 bits; entries below 2^-103 of the call's largest entry count as 0,
+ * far below the tolerance.  NaN and +-inf in the input give NaN / +-inf in the
+ * outputs they reach (as in FP64), so a CG solve from a non-finite x0 returns
+ * SIPG_NONFINITE.  Scalar coefficients (mass_coef, nu, mass_coef / nu) must
+ * be 0 or lie in [2^-100, 2^100] in magnitude, else the call returns
+ * SIPG_EINVAL (use SIPG_F64_NATIVE); per-cell coefficient arrays (nu_cell, tau)
+ * are converted unscaled: their nonzero entries must lie in [2^-100, 2^126].
+ * The scale lives in a 16-byte word of the mesh (allocated by
+ * sipg_create_mesh), so double-float calls on one mesh must be ordered on the
+ * GPU (one stream, or streams joined by events). */
 int sipg_set_f64_arithmetic(sipg_mesh* mesh, int mode);
 int sipg_get_f64_arithmetic(const sipg_mesh* mesh, int* mode);
 

@@ -43,6 +43,7 @@ Mesh::~Mesh() {
   if (dconv64) cudaFree(dconv64);
   if (dconvdf) cudaFree(dconvdf);
   if (dns64) cudaFree(dns64);
+  if (dscale) cudaFree(dscale);
   for (double* q : {dgen_head, dgen_geo, dgen_face, dgen_tau})
     if (q) cudaFree(q);
   for (auto& pr : pending) {
@@ -69,6 +70,7 @@ Geo<T> make_geo(const Mesh& m) {
       g.tab[d] = reinterpret_cast<const T*>(m.dtabdf[d]);
   }
   g.tau_scale = T(m.penalty * (m.k + 1) * (m.k + 1));
+  g.dsc = m.dscale ? m.dscale + 2 : nullptr;
   return g;
 }
 template Geo<double> make_geo<double>(const Mesh&);
@@ -229,6 +231,13 @@ int sipg_create_mesh(const sipg_mesh_desc* d, sipg_mesh** out) {
   }
   m->k = 3;
   m->p = 4;
+  e = cudaMalloc(&m->dscale, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->dscale, 0, 4 * sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return fail(SIPG_ENOMEM, "cudaMalloc of the mesh's scale word failed");
+  }
   int st = build_tables(*m);
   if (st) {
     delete m;

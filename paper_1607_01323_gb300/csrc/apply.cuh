@@ -34,22 +34,33 @@
 namespace sipg {
 
 // storage <-> compute conversions (identity unless FP64 data is computed in
-// double-float)
+// double-float).  sc is the call's scale exponent: data enter as v 2^-sc and
+// leave as v 2^sc (a product of two scaled data leaves with 2 sc);
+// coefficients and geometry convert unscaled (sc = 0).
 template <typename T, typename S>
-__device__ __forceinline__ T cvt_in(S v) {
+__device__ __forceinline__ T cvt_in(S v, int sc = 0) {
   return (T)v;
 }
 template <>
-__device__ __forceinline__ dfl cvt_in<dfl, double>(double v) {
-  return df_from_double(v);
+__device__ __forceinline__ dfl cvt_in<dfl, double>(double v, int sc) {
+  return df_from_double(v, sc);
 }
 template <typename S, typename T>
-__device__ __forceinline__ S cvt_out(T v) {
+__device__ __forceinline__ S cvt_out(T v, int sc = 0) {
   return (S)v;
 }
 template <>
-__device__ __forceinline__ double cvt_out<double, dfl>(dfl v) {
-  return df_to_double(v);
+__device__ __forceinline__ double cvt_out<double, dfl>(dfl v, int sc) {
+  return df_to_double(v, sc);
+}
+
+// the call's scale exponent (double-float kernels only)
+template <typename T>
+__device__ __forceinline__ int call_scale(const Geo<T>& g) {
+  if constexpr (std::is_same<T, dfl>::value)
+    return g.dsc ? *g.dsc : 0;
+  else
+    return 0;
 }
 
 template <int P>
@@ -296,9 +307,10 @@ __device__ __forceinline__ void load_line_global(T (&v)[P], const T* __restrict_
 }
 
 template <typename T, typename S, int P>
-__device__ __forceinline__ void load_line_global_cvt(T (&v)[P], const S* __restrict__ base, int start, int step) {
+__device__ __forceinline__ void load_line_global_cvt(T (&v)[P], const S* __restrict__ base, int start, int step,
+                                                     int sc) {
 #pragma unroll
-  for (int a = 0; a < P; ++a) v[a] = cvt_in<T, S>(__ldg(base + start + a * step));
+  for (int a = 0; a < P; ++a) v[a] = cvt_in<T, S>(__ldg(base + start + a * step), sc);
 }
 
 template <typename T, int P>
@@ -445,10 +457,11 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
   const bool active = cs < cpb && e < g.ncell;  // blocks are rounded up to whole warps
   const long long cbase = (long long)blockIdx.y * g.ncell * P3;
   const S* __restrict__ xc = x + cbase;
+  const int sc = call_scale(g);
   {
     const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
     const S* xb = xc + cell0 * P3;
-    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx]);
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx], sc);
   }
   __syncthreads();
   T* us = su + cs * P3;
@@ -480,8 +493,8 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
       }
       if (stiff) {
         DirCtx<T, P> c = dir_ctx<T, P, S>(g, dir, id, e, nue, tau_e, nu_cell, nu);
-        if (c.kindL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)c.nbL * P3, start, step);
-        if (c.kindR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)c.nbR * P3, start, step);
+        if (c.kindL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)c.nbL * P3, start, step, sc);
+        if (c.kindR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)c.nbR * P3, start, step, sc);
         line_op<T, P>(w, u, c.L, nue, true, T(0), false, c.kindL, uL, c.LL, c.nuL, c.tauFL, c.kindR, uR, c.LR, c.nuR,
                       c.tauFR, tau_e);
       } else {
@@ -499,8 +512,8 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
     load_line<T, P>(u, us, start, step);
     DirCtx<T, P> c = dir_ctx<T, P, S>(g, 2, id, e, nue, tau_e, nu_cell, nu);
     if (stiff) {
-      if (c.kindL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)c.nbL * P3, start, step);
-      if (c.kindR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)c.nbR * P3, start, step);
+      if (c.kindL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)c.nbL * P3, start, step, sc);
+      if (c.kindR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)c.nbR * P3, start, step, sc);
     }
     line_op<T, P>(w, u, c.L, nue, stiff, mass_coef, mass_coef != T(0), c.kindL, uL, c.LL, c.nuL, c.tauFL, c.kindR, uR,
                   c.LR, c.nuR, c.tauFR, tau_e);
@@ -542,7 +555,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
 #pragma unroll
     for (int a = 0; a < P; ++a) {
       out[a] += r1[a];
-      yo[a] = cvt_out<S, T>(out[a]);
+      yo[a] = cvt_out<S, T>(out[a], sc);
     }
     if (dots) {
       T sxy(0), sy(0), sx(0);
@@ -555,9 +568,9 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
           sx += ux[a];
         }
       }
-      d_xy = cvt_out<double, T>(sxy);
-      d_y = cvt_out<double, T>(sy);
-      d_x = cvt_out<double, T>(sx);
+      d_xy = cvt_out<double, T>(sxy, 2 * sc);
+      d_y = cvt_out<double, T>(sy, sc);
+      d_x = cvt_out<double, T>(sx, sc);
     }
   }
   if (dots) sink_dots(sink, d_xy, d_y, d_x);
@@ -639,9 +652,10 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   const long long cbase = (long long)blockIdx.y * g.ncell * P3;
   const S* __restrict__ xc = x + cbase;
   const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);  // cells staged in this block
+  const int sc = call_scale(g);
   {
     const S* xb = xc + cell0 * P3;
-    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx]);
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx], sc);
   }
   __syncthreads();
   T* us = su + cs * P3;
@@ -676,14 +690,14 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
         if (sl >= 0 && sl < nc)
           load_line<T, P>(uL, su + sl * P3, start, step);
         else
-          load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step);
+          load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step, sc);
       }
       if (kR == 0) {
         const long long sr = (long long)nbR - cell0;
         if (sr >= 0 && sr < nc)
           load_line<T, P>(uR, su + sr * P3, start, step);
         else
-          load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step);
+          load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
       }
       line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
                       kR == 0 ? g.tab[dir] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
@@ -711,8 +725,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     face_neighbor(g, 2, 1, id[2], e, nbR, kR, jr);
     T u[P], uL[P], uR[P], w[P];
     load_line<T, P>(u, us, start, step);
-    if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step);
-    if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step);
+    if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step, sc);
+    if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
     line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
                     kR == 0 ? g.tab[2] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
     if (do_mass) {
@@ -771,7 +785,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
       for (int a = 0; a < P; ++a) {
         out[a] += r1[a];
         if (do_scale) out[a] *= scale;
-        yo[a] = cvt_out<S, T>(out[a]);
+        yo[a] = cvt_out<S, T>(out[a], sc);
       }
     }
     if (!CHEB && dots) {
@@ -789,9 +803,9 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
           sx += ux[a];
         }
       }
-      d_xy = cvt_out<double, T>(sxy);
-      d_y = cvt_out<double, T>(sy);
-      d_x = cvt_out<double, T>(sx);
+      d_xy = cvt_out<double, T>(sxy, 2 * sc);
+      d_y = cvt_out<double, T>(sy, sc);
+      d_x = cvt_out<double, T>(sx, sc);
     }
   }
   if (dots) sink_dots(sink, d_xy, d_y, d_x);
@@ -1016,10 +1030,11 @@ __global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<T> g,
   const int e = (int)(cell0 + cs);
   const bool active = cs < cpb && e < g.ncell;  // blocks are rounded up to whole warps
   const long long cbase = (long long)blockIdx.y * g.ncell * P3;
+  const int sc = call_scale(g);
   {
     const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
     const S* xb = x + cbase + cell0 * P3;
-    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx]);
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx], sc);
   }
   __syncthreads();
   T* us = su + cs * P3;
@@ -1049,19 +1064,19 @@ __global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<T> g,
     load_line<T, P>(v, us, start, step);
     matvec(o, g.tab[0] + id[0] * O::stride + O::Mi, v);
     const long long off = cbase + (long long)e * P3 + start;
-    for (int a = 0; a < P; ++a) y[off + a] = cvt_out<S, T>(o[a]);
+    for (int a = 0; a < P; ++a) y[off + a] = cvt_out<S, T>(o[a], sc);
     if (dots) {
       T xv[P];
-      load_line_global_cvt<T, S, P>(xv, x + cbase + (long long)e * P3, start, step);
+      load_line_global_cvt<T, S, P>(xv, x + cbase + (long long)e * P3, start, step, sc);
       T sxy(0), sy(0), sx(0);
       for (int a = 0; a < P; ++a) {
         sxy = fma(o[a], xv[a], sxy);
         sy += o[a];
         sx += xv[a];
       }
-      d_xy = cvt_out<double, T>(sxy);
-      d_y = cvt_out<double, T>(sy);
-      d_x = cvt_out<double, T>(sx);
+      d_xy = cvt_out<double, T>(sxy, 2 * sc);
+      d_y = cvt_out<double, T>(sy, sc);
+      d_x = cvt_out<double, T>(sx, sc);
     }
   }
   if (dots) block_reduce3(d_xy, d_y, d_x, dots + 3 * ((long long)blockIdx.y * gridDim.x + blockIdx.x));

@@ -54,6 +54,12 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
     const int do_scale = nu != T(1) ? 1 : 0, do_mass = cm != T(0) ? 1 : 0;
     if constexpr (std::is_same<T, double>::value) {
       if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
+        if (!df_coef_ok(cm / nu) || !df_coef_ok(nu))
+          return fail(SIPG_EINVAL, "double-float arithmetic needs mass_coef / nu and nu in [2^-100, 2^100]");
+        if (!ds.prescaled) {
+          const int st = launch_df_scale(m, x, m.ncell * P * P * P * ncomp, nullptr, 0, ds.skip, s);
+          if (st) return st;
+        }
         const Geo<dfl> gd = make_geo<dfl>(m);
         if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
           cudaError_t e = cudaFuncSetAttribute(apply_uniform_kernel<dfl, double, P>,
@@ -73,6 +79,12 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
   } else {
     if constexpr (std::is_same<T, double>::value) {
       if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
+        if (!df_coef_ok(cm) || !df_coef_ok(nu))
+          return fail(SIPG_EINVAL, "double-float arithmetic needs mass_coef and nu in [2^-100, 2^100]");
+        if (!ds.prescaled) {
+          const int st = launch_df_scale(m, x, m.ncell * P * P * P * ncomp, nullptr, 0, ds.skip, s);
+          if (st) return st;
+        }
         if (smem + 2048 > 48 * 1024) {
           cudaError_t e = cudaFuncSetAttribute(apply_kernel<dfl, double, P>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -24,7 +24,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <vector>
 
 #include "sipg_internal.h"
@@ -398,13 +397,20 @@ __global__ void k_set_rz2(Scalars* sc, const double* __restrict__ part1, int nb1
   }
 }
 
-// p = z + beta p   (beta = 0 with init != 0: p = z)
+// p = z + beta p   (beta = 0 with init != 0: p = z).  With dsc set, also the
+// double-float scale of the new p for the operator that reads it next
+// (df_scale_reduce), which then needs no scale pass of its own.
 __global__ void k_pupdate(const Scalars* __restrict__ sc, long long n, double* __restrict__ p,
-                          const double* __restrict__ z, int init) {
+                          const double* __restrict__ z, int init, int* __restrict__ dsc) {
   if (sc->done) return;
   const double beta = init ? 0.0 : sc->beta;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    p[i] = init ? z[i] : fma(beta, p[i], z[i]);
+  int key = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = init ? z[i] : fma(beta, p[i], z[i]);
+    p[i] = v;
+    if (dsc) key = max(key, df_scale_key(v));
+  }
+  if (dsc) df_scale_reduce(key, dsc);
 }
 
 // x.y of the operator's input and output with the last block forming the
@@ -635,8 +641,10 @@ struct Solver {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
   int ev_used = 0;
   bool capturing = false;
+  bool prof;  // per-apply timing events (the mesh's profiling setting)
 
-  Solver(Mesh& mm, const sipg_cg_opts& oo, int nc, cudaStream_t ss) : m(mm), o(oo), ncomp(nc), s(ss) {
+  Solver(Mesh& mm, const sipg_cg_opts& oo, int nc, cudaStream_t ss)
+      : m(mm), o(oo), ncomp(nc), s(ss), prof(mm.profile) {
     n = (long long)m.ncell * m.p * m.p * m.p * ncomp;
     helm = o.op == SIPG_OP_HELMHOLTZ;
     visc = o.op == SIPG_OP_VISCOUS;
@@ -651,16 +659,23 @@ struct Solver {
     return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "CG kernel launch");
   }
 
+  // the search direction's double-float scale comes from k_pupdate (operators
+  // of the separable kernels only; the others run their own scale pass)
+  int* pscale() const {
+    return (m.f64_arith == SIPG_F64_DOUBLE_FLOAT && !visc && !m.general()) ? m.dscale : nullptr;
+  }
+
   int apply64(const double* x, double* y, double* dots, int* nb) {
     DotSink sink;
     sink.partials = dots;
+    sink.prescaled = (x == w.p && pscale()) ? 1 : 0;
     if (dots) {  // inside an iteration: the last block forms the totals; skip once the solver is done
       sink.counter = &w.sc->cnt_apply;
       sink.totals = w.sc->tot;
       sink.skip = &w.sc->done;
       sink.sums = o.zero_mean ? 1 : 0;
     }
-    if (m.profile) {
+    if (prof) {
       if (ev_used >= (int)evs.size()) {
         std::pair<cudaEvent_t, cudaEvent_t> pr;
         cudaEventCreate(&pr.first);
@@ -695,7 +710,7 @@ struct Solver {
     } else {
       st = launch_apply<double>(m, x, y, ncomp, cm, nu, nu_cell, true, dots ? &sink : nullptr, nb, s);
     }
-    if (m.profile) {
+    if (prof) {
       cudaEventRecordWithFlags(evs[ev_used].second, s, capturing ? cudaEventRecordExternal : 0);
       ++ev_used;
     }
@@ -776,7 +791,7 @@ struct Solver {
       k_beta<<<1, kRedThreads, 0, s>>>(w.sc, w.part1, kVecBlocks, w.part2, nb2, flex);
       if ((st = launched())) return st;
     }
-    k_pupdate<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, w.p, z, 0);
+    k_pupdate<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, w.p, z, 0, pscale());
     return launched();
   }
 
@@ -790,7 +805,7 @@ struct Solver {
     if (e != cudaSuccess) return cuda_fail(e, "read CG state");
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "CG synchronise");
-    if (m.profile) {
+    if (prof) {
       harvest(first_read ? ev_used : h.iters - iters_seen);
       first_read = false;
     }
@@ -835,7 +850,7 @@ struct Solver {
       k_set_rz<<<1, kRedThreads, 0, s>>>(w.sc, w.part1, kVecBlocks);
     }
     if ((st = launched())) return st;
-    k_pupdate<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, w.p, z, 1);
+    k_pupdate<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, w.p, z, 1, pscale());
     if ((st = launched())) return st;
     (void)nb;
     int done = 0, iters = 0;
@@ -877,7 +892,7 @@ struct Solver {
           return cuda_fail(e, "cudaGraphLaunch");
         }
         m.launches += graph_kernels;
-        if (m.profile) ev_used = chunk < (int)evs.size() ? chunk : (int)evs.size();
+        if (prof) ev_used = chunk < (int)evs.size() ? chunk : (int)evs.size();
       } else {
         for (int i = 0; i < chunk; ++i)
           if ((st = iteration())) return st;
@@ -1020,32 +1035,25 @@ int cg_solve(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int nco
 // CG without allocation: the same solver, with its workspace carved out of a
 // fixed device array instead of cudaMalloc'd memory.
 //
-// The array below is a file-scope __device__ object: every GPU that loads the
-// library holds these kNoAllocScratchBytes until the process exits, whether or
-// not the entry point is ever called.  In host code its name is only a host-side
-// stand-in; the device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and cached.  Every call
-// shares the array, so calls that overlap on the GPU (different streams, host
-// threads or devices sharing a context) race on it.
+// The array below is a file-scope __device__ object: a GPU holds these
+// kNoAllocScratchBytes from the moment this file's module is loaded on it
+// (with CUDA's lazy module loading that can be the first call of the entry
+// point itself, a driver-side reservation) until the process exits.  In host
+// code its name is only a host-side stand-in; every call looks up the device
+// address with cudaGetSymbolAddress, with the mesh's device current, so the
+// address stays right after a context is torn down and re-created.  Every
+// call shares the array, so calls that overlap on the GPU (different streams,
+// host threads or devices sharing a context) race on it.
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[kMaxDevices] = {nullptr};
-
-int noalloc_scratch(int device, void** out) {
-  if (device < 0 || device >= kMaxDevices) return fail(SIPG_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static CG scratch)");
-    g_noalloc_ptr[device] = p;
-  }
-  *out = g_noalloc_ptr[device];
+int noalloc_scratch(void** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static CG scratch)");
+  *out = p;
   return SIPG_OK;
 }
 
@@ -1081,7 +1089,7 @@ int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o_in, const double* b, double*
     return fail(SIPG_EINVAL, msg);
   }
   void* base_v = nullptr;
-  int st = noalloc_scratch(m.device, &base_v);
+  int st = noalloc_scratch(&base_v);
   if (st) return st;
   char* base = (char*)base_v;
   Workspace w;
@@ -1100,12 +1108,12 @@ int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o_in, const double* b, double*
   cudaError_t e = cudaMemsetAsync(w.sc, 0, sizeof(Scalars), s);
   if (e != cudaSuccess) return cuda_fail(e, "clear static CG scratch");
   // run on the caller's stream, without a CUDA graph and without profiling
-  // events (their creation would allocate)
+  // events (their creation would allocate); the mesh's own profiling setting
+  // is left untouched
   sipg_cg_opts o = o_in;
   o.use_graph = 0;
-  const bool prof = m.profile;
-  m.profile = false;
   Solver S(m, o, ncomp, s);
+  S.prof = false;
   S.w = w;
   const bool helm = o.op == SIPG_OP_HELMHOLTZ;
   const double cm = helm ? o.mass_coef : 0.0, nu = helm ? o.nu : 1.0;
@@ -1120,7 +1128,6 @@ int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o_in, const double* b, double*
     }
   }
   if (!st) st = S.run(b, x, o.maxit, o.rtol, false, &it, &rel, &done);
-  m.profile = prof;
   if (st) return st;
   if (iters) *iters = it;
   if (relres) *relres = rel;

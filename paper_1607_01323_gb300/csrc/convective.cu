@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kConvThreads) convective_kernel(Geo<T> g, cons
                                                                   double* __restrict__ y, int cpb) {
   using Dm = ConvDims<P>;
   constexpr int Q = Dm::Q, P2 = Dm::P2, P3 = Dm::P3, Q2 = Dm::Q2, Q3 = Dm::Q3, PC = Dm::per_cell;
+  const int sc = call_scale(g);  // data enter as u 2^-sc; the result leaves with 2^(2 sc)
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Sq = reinterpret_cast<T*>(smraw);  // Sq[q * P + a] = l_a(z_q)
   T* Dq = Sq + Q * P;                    // Dq[a * Q + q] = w_q l_a'(z_q)
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(kConvThreads) convective_kernel(Geo<T> g, cons
   }
   for (int i = threadIdx.x; i < cpb * 3 * P3; i += NT) {
     const int lc = i / (3 * P3), r = i % (3 * P3), e = e0 + lc;
-    SU(lc)[r] = e < g.ncell ? cvt_in<T, double>(u[(r / P3) * N + (long long)e * P3 + r % P3]) : T(0);
+    SU(lc)[r] = e < g.ncell ? cvt_in<T, double>(u[(r / P3) * N + (long long)e * P3 + r % P3], sc) : T(0);
   }
   __syncthreads();
 
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kConvThreads) convective_kernel(Geo<T> g, cons
       v = SU(lc)[c * P3 + aend * nstride<P>(d) + tr];
     } else if (fkind[lc * 6 + f] == 0) {
       const int nend = P - 1 - aend;
-      v = cvt_in<T, double>(u[c * N + (long long)fnb[lc * 6 + f] * P3 + nend * nstride<P>(d) + tr]);
+      v = cvt_in<T, double>(u[c * N + (long long)fnb[lc * 6 + f] * P3 + nend * nstride<P>(d) + tr], sc);
     }
     XB(lc)[r] = v;
   }
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(kConvThreads) convective_kernel(Geo<T> g, cons
       const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
       v = v - XB(lc)[(f * 3 + c) * P2 + ax[t2] * P + ax[t1]];
     }
-    y[c * N + (long long)e * P3 + node] = cvt_out<double, T>(v);
+    y[c * N + (long long)e * P3 + node] = cvt_out<double, T>(v, 2 * sc);  // quadratic in u
   }
 #undef SU
 #undef SO
@@ -405,6 +406,10 @@ int launch_convective_p(const Mesh& m, const double* u, double* y, cudaStream_t 
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(convective)");
   }
   const unsigned blocks = (unsigned)((m.ncell + cpb - 1) / cpb);
+  if (df) {
+    const int st = launch_df_scale(m, u, 3 * m.ncell * P * P * P, nullptr, 0, nullptr, s);
+    if (st) return st;
+  }
   if (df)
     convective_kernel<dfl, P><<<blocks, kConvThreads, smem, s>>>(
         make_geo<dfl>(m), m.dconvdf, (int)m.conv_off[1], (int)m.conv_off[2], (int)m.conv_off[3],

@@ -260,7 +260,9 @@ __global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a
   const int nt = blockDim.x, tid = threadIdx.x;
   const long long N = (long long)a.g.ncell * P3;
   const double* x = a.x + comp * N;
-  for (int i = tid; i < P3; i += nt) su[i] = cvt_in<T, double>(x[(long long)e * P3 + i]);
+  int sc = 0;  // the call's scale exponent (double-float)
+  if constexpr (std::is_same<T, dfl>::value) sc = a.g.dsc ? *a.g.dsc : 0;
+  for (int i = tid; i < P3; i += nt) su[i] = cvt_in<T, double>(x[(long long)e * P3 + i], sc);
   for (int i = tid; i < P2; i += nt) {
     sS[i] = cvt_in<T, double>(a.head[i]);
     sD[i] = cvt_in<T, double>(a.head[P2 + i]);
@@ -406,9 +408,9 @@ __global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a
         fv[1][j] = nd;
         if (kind == 0) {
           const double* xn = x + (long long)nb * P3;
-          fv[2][j] = cvt_in<T, double>(xn[nend * sd + tr]);
+          fv[2][j] = cvt_in<T, double>(xn[nend * sd + tr], sc);
           T nn = T(0);
-          for (int i = 0; i < P; ++i) nn = fma(dnb[i], cvt_in<T, double>(xn[i * sd + tr]), nn);
+          for (int i = 0; i < P; ++i) nn = fma(dnb[i], cvt_in<T, double>(xn[i * sd + tr], sc), nn);
           fv[3][j] = nn;
         }
       }
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a
     }
   }
   double* y = a.y + comp * N;
-  for (int i = tid; i < P3; i += nt) y[(long long)e * P3 + i] = cvt_out<double, T>(W[i]);
+  for (int i = tid; i < P3; i += nt) y[(long long)e * P3 + i] = cvt_out<double, T>(W[i], sc);
 }
 
 // diag(A)_i = a(phi_i, phi_i) on a general map: the cell term summed over the
@@ -628,6 +630,12 @@ int launch_general(const Mesh& m, const double* x, double* y, int ncomp, double 
   a.stiffness = stiffness ? 1 : 0;
   a.skip = skip;
   const dim3 grid((unsigned)m.ncell, (unsigned)ncomp);
+  if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
+    if (!df_coef_ok(cm) || !df_coef_ok(nu))
+      return fail(SIPG_EINVAL, "double-float arithmetic needs mass_coef and nu in [2^-100, 2^100]");
+    const int st = launch_df_scale(m, x, m.ncell * m.p * m.p * m.p * ncomp, nullptr, 0, skip, s);
+    if (st) return st;
+  }
   switch (m.p) {
 #define SIPG_GEN_CASE(P) \
   case P:                \

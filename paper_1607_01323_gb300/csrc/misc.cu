@@ -1,9 +1,29 @@
-// Inverse mass, diagonal and adjoint-gradient launchers (FP64).
+// Inverse mass, diagonal and adjoint-gradient launchers (FP64), and the scale
+// pass of the double-float calls.
+#include <cmath>
+
 #include "adjoint.cuh"
 
 namespace sipg {
 
 namespace {
+
+constexpr int kScaleThreads = 256, kScaleBlocks = 152 * 4;
+
+// Largest df_scale_key over v[0..n) and v2[0..n2) into the scale word
+// (df_scale_reduce).
+__global__ void __launch_bounds__(kScaleThreads) df_scale_kernel(const double* __restrict__ v, long long n,
+                                                                 const double* __restrict__ v2, long long n2,
+                                                                 int* __restrict__ dsc, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  int key = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long i = t0; i < n; i += stride) key = max(key, df_scale_key(__ldg(v + i)));
+  if (v2)
+    for (long long i = t0; i < n2; i += stride) key = max(key, df_scale_key(__ldg(v2 + i)));
+  df_scale_reduce(key, dsc);
+}
 
 template <int P>
 int launch_inverse_mass_p(const Mesh& m, const double* x, double* y, int ncomp, double* dots, cudaStream_t s) {
@@ -14,6 +34,8 @@ int launch_inverse_mass_p(const Mesh& m, const double* x, double* y, int ncomp, 
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
   // same arithmetic choice as the operator (double-float keeps FP64 data)
   if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
+    const int st = launch_df_scale(m, x, m.ncell * P * P * P * ncomp, nullptr, 0, nullptr, s);
+    if (st) return st;
     if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
       cudaError_t e = cudaFuncSetAttribute(inverse_mass_kernel<dfl, double, P>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -47,6 +69,23 @@ int launch_diagonal_p(const Mesh& m, bool stiffness, double cm, double nu, const
 }
 
 }  // namespace
+
+int launch_df_scale(const Mesh& m, const double* v, long long n, const double* v2, long long n2, const int* skip,
+                    cudaStream_t s) {
+  if (!m.dscale) return fail(SIPG_EINVAL, "mesh has no scale word");
+  const long long work = (n > n2 ? n : n2) / 4;  // a few elements per thread
+  long long blocks = (work + kScaleThreads - 1) / kScaleThreads;
+  blocks = blocks < 1 ? 1 : (blocks > kScaleBlocks ? kScaleBlocks : blocks);
+  df_scale_kernel<<<(unsigned)blocks, kScaleThreads, 0, s>>>(v, n, v2, v2 ? n2 : 0, m.dscale, skip);
+  const_cast<Mesh&>(m).launches++;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "double-float scale pass launch");
+}
+
+bool df_coef_ok(double v) {
+  const double a = std::fabs(v);
+  return a == 0.0 || (a >= 0x1p-100 && a <= 0x1p100);
+}
 
 #define SIPG_DISPATCH_P(FN, ...)                       \
   switch (m.p) {                                       \

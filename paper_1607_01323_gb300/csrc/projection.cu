@@ -381,12 +381,16 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
   double* red = reinterpret_cast<double*>(Pk + 3 * P * P);  // 32
   const int e = blockIdx.x;
   const long long N = (long long)g.ncell * P3;
+  // the call's scale exponent covers rhs and the initial x: vectors in T hold
+  // v 2^-sc; r.r is compared with the unscaled bb (2 sc), the other dot
+  // products only enter ratios
+  const int sc = call_scale(g);
   double bb = 0.0;
   for (int i = threadIdx.x; i < V; i += blockDim.x) {
     const long long gi = (i / P3) * N + (long long)e * P3 + i % P3;
-    sx[i] = cvt_in<T, double>(x[gi]);
+    sx[i] = cvt_in<T, double>(x[gi], sc);
     const double b = rhs[gi];
-    sr[i] = cvt_in<T, double>(b);
+    sr[i] = cvt_in<T, double>(b, sc);
     bb += b * b;
   }
   stage_c<P>(Cg, C, Ct);
@@ -403,7 +407,7 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
     acc = fma(sr[i], sr[i], acc);
   }
   __syncthreads();
-  double rr = block_sum(cvt_out<double, T>(acc), red);
+  double rr = block_sum(cvt_out<double, T>(acc, 2 * sc), red);
   blockprec_cell<P>(cc, Pk, sr, sz, t1, t2);
   acc = T(0);
   for (int i = threadIdx.x; i < V; i += blockDim.x) {
@@ -433,7 +437,7 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
       acc = fma(sr[i], sr[i], acc);
     }
     __syncthreads();
-    rr = block_sum(cvt_out<double, T>(acc), red);
+    rr = block_sum(cvt_out<double, T>(acc, 2 * sc), red);
     blockprec_cell<P>(cc, Pk, sr, sz, t1, t2);
     acc = T(0);
     for (int i = threadIdx.x; i < V; i += blockDim.x) acc = fma(sr[i], sz[i], acc);
@@ -445,7 +449,7 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
     ++it;
   }
   for (int i = threadIdx.x; i < V; i += blockDim.x)
-    x[(i / P3) * N + (long long)e * P3 + i % P3] = cvt_out<double, T>(sx[i]);
+    x[(i / P3) * N + (long long)e * P3 + i % P3] = cvt_out<double, T>(sx[i], sc);
   if (threadIdx.x == 0) {
     if (broke) atomicOr(status, 2);
     else if (rr > tol2) atomicOr(status, 1);
@@ -488,8 +492,9 @@ __global__ void viscous_t_kernel(Geo<T> g, const T* __restrict__ Cg, const doubl
   T* fb = Ct + P2;  // face arrays [11][P2]
   const int e = blockIdx.x;
   const long long N = (long long)g.ncell * P3;
+  const int xsc = call_scale(g);  // the call's scale exponent (double-float)
   for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x)
-    su[i] = cvt_in<T, double>(u[(i / P3) * N + (long long)e * P3 + i % P3]);
+    su[i] = cvt_in<T, double>(u[(i / P3) * N + (long long)e * P3 + i % P3], xsc);
   stage_c<P>(Cg, C, Ct);
   __syncthreads();
   const CellCtxT<T> cc = cell_ctx<P>(g, e, (const T*)C, (const T*)Ct);
@@ -541,10 +546,10 @@ __global__ void viscous_t_kernel(Geo<T> g, const T* __restrict__ Cg, const doubl
           const double* un = u + (long long)nb * P3 + base;
           T g_nb = T(0);
 #pragma unroll
-          for (int a = 0; a < P; ++a) g_nb = fma(dN[a], cvt_in<T, double>(un[d * N + a * sd]), g_nb);
-          const T udn = cvt_in<T, double>(un[d * N + nend * sd]);
-          const T uan = cvt_in<T, double>(un[ta * N + nend * sd]);
-          const T ubn = cvt_in<T, double>(un[tb * N + nend * sd]);
+          for (int a = 0; a < P; ++a) g_nb = fma(dN[a], cvt_in<T, double>(un[d * N + a * sd], xsc), g_nb);
+          const T udn = cvt_in<T, double>(un[d * N + nend * sd], xsc);
+          const T uan = cvt_in<T, double>(un[ta * N + nend * sd], xsc);
+          const T ubn = cvt_in<T, double>(un[tb * N + nend * sd], xsc);
           avgN = T(0.5) * (g_own + g_nb);
           avgU = T(0.5) * (ud + udn);
           Jd = ud - udn;
@@ -615,7 +620,7 @@ __global__ void viscous_t_kernel(Geo<T> g, const T* __restrict__ Cg, const doubl
   const T sc = T(scale);
   for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x) {
     const long long gi = (i / P3) * N + (long long)e * P3 + i % P3;
-    y[gi] = y[gi] + cvt_out<double, T>(sc * so[i]);
+    y[gi] = y[gi] + cvt_out<double, T>(sc * so[i], xsc);
   }
 }
 
@@ -692,6 +697,10 @@ int launch_divdiv_solve_p(const Mesh& m, const double* tau, const double* rhs, d
                                   (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(div-div solve)");
   }
+  if (df) {
+    const int st = launch_df_scale(m, rhs, 3 * m.ncell * P3, x, 3 * m.ncell * P3, nullptr, s);
+    if (st) return st;
+  }
   if (df)
     divdiv_solve_kernel<dfl, P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<dfl>(m), m.dCdf, tau,
                                                                                  rhs, x, rtol, maxit, status);
@@ -714,6 +723,11 @@ int launch_viscous_t_p(const Mesh& m, const double* u, double* y, double scale, 
             : cudaFuncSetAttribute(viscous_t_kernel<double, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(viscous coupling)");
+  }
+  if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
+    if (!df_coef_ok(scale)) return fail(SIPG_EINVAL, "double-float arithmetic needs nu in [2^-100, 2^100]");
+    const int st = launch_df_scale(m, u, 3 * m.ncell * P3, nullptr, 0, skip, s);
+    if (st) return st;
   }
   if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT)
     viscous_t_kernel<dfl, P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<dfl>(m), m.dCdf, u, y, scale,

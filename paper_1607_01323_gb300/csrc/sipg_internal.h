@@ -64,6 +64,7 @@ struct Geo {
   int ncell;
   const T* tab[3];  // per-direction layer tables on the device
   T tau_scale;      // penalty factor * (k+1)^2
+  const int* dsc;   // scale exponent of the call (double-float kernels; see launch_df_scale)
 };
 
 // Host-side state of one mesh.
@@ -116,6 +117,9 @@ struct Mesh {
   long long prof_applies = 0;
   long long launches = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // unread event pairs
+  // double-float scale word [key accumulator, block counter, scale exponent, -]
+  // written by launch_df_scale before every double-float kernel of a call
+  int* dscale = nullptr;
   // cached CG workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -165,6 +169,7 @@ struct DotSink {
   double* totals = nullptr;
   const int* skip = nullptr;
   int sums = 1;  // 0: only x.y is needed (sum y, sum x are left 0)
+  int prescaled = 0;  // 1: the kernel that wrote x already left its double-float scale in the mesh's word
 };
 
 // Chebyshev-step epilogue of the FP32 Laplace operator (multigrid smoother):
@@ -192,6 +197,17 @@ int launch_apply<double>(const Mesh& m, const double* x, double* y, int ncomp, d
 template <>
 int launch_apply<float>(const Mesh& m, const float* x, float* y, int ncomp, float mass_coef, float nu,
                         const float* nu_cell, bool stiffness, const DotSink* sink, int* nblocks, cudaStream_t s);
+
+// Scale pass of a double-float call: the scale exponent s of the finite
+// entries of v[0..n) and v2[0..n2) (v2 may be null) into m.dscale[2], so that
+// the call's kernels evaluate v 2^-s and scale their results back exactly.
+// Returns at once when skip is set and *skip != 0.  Calls on one mesh share
+// the word, so double-float calls on one mesh must be stream-ordered.
+int launch_df_scale(const Mesh& m, const double* v, long long n, const double* v2, long long n2, const int* skip,
+                    cudaStream_t s);
+// A scalar coefficient of a double-float call must be 0 or lie in
+// [2^-100, 2^100] in magnitude (the FP32 exponent range with room to spare).
+bool df_coef_ok(double v);
 
 int launch_inverse_mass(const Mesh& m, const double* x, double* y, int ncomp, double* dots, const double* rdot,
                         cudaStream_t s);

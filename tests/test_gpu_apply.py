@@ -121,14 +121,116 @@ def test_double_float_dynamic_range():
     assert scaled_err(y, A @ x, abs(A).sum(axis=1).max(), x) <= TOL64
 
 
+# magnitudes across the FP64 range: subnormals, far below and far above the
+# FP32 exponent range, and a vector mixing 1e-150 with 1e150
+EXTREME = [("subnormal", 1e-310), ("1e-200", 1e-200), ("1e-30", 1e-30), ("1e30", 1e30), ("1e200", 1e200),
+           ("mixed_1e-150_1e150", None)]
+
+
+@pytest.mark.parametrize("name,scale", EXTREME, ids=[e[0] for e in EXTREME])
+def test_double_float_extreme_magnitudes(name, scale):
+    """The double-float evaluation scales each call's input by a power of two,
+    so FP64 data anywhere in the FP64 range keep the 1e-12 bar (Laplace,
+    Helmholtz, per-cell viscosity, inverse mass), like native FP64."""
+    from paper_1607_01323_gb300 import apply_helmholtz_f64, apply_inverse_mass_f64, apply_laplace_f64
+    c = channel((3, 4, 2))
+    k = 4
+    op = SIPG(oracle_spec(c), k)
+    m = gpu_mesh(c, k)
+    m.set_f64_arithmetic("double_float")
+    N = m.n_dofs
+    x = uniform(N, "x")
+    if scale is None:
+        x[::2] *= 1e-150
+        x[1::2] *= 1e150
+    else:
+        x = x * scale
+    A = op.assemble()
+    y = apply_laplace_f64(m, _cuda(x)).cpu().numpy()
+    assert np.all(np.isfinite(y))
+    assert scaled_err(y, A @ x, abs(A).sum(axis=1).max(), x) <= TOL64
+    cm, nu = 1500.0, 1.0 / 180.0
+    H = op.assemble(mass_coef=cm, nu=nu)
+    yh = apply_helmholtz_f64(m, _cuda(x), cm, nu).cpu().numpy()
+    assert scaled_err(yh, H @ x, abs(H).sum(axis=1).max(), x) <= TOL64
+    nu_cell = np.exp(0.5 * inputs.normal(0, "xi", m.ncell)) / 180.0
+    Hc = op.assemble(mass_coef=cm, nu_cell=nu_cell)
+    yc = apply_helmholtz_f64(m, _cuda(x), cm, 0.0, nu_cell=_cuda(nu_cell)).cpu().numpy()
+    assert scaled_err(yc, Hc @ x, abs(Hc).sum(axis=1).max(), x) <= TOL64
+    yi = apply_inverse_mass_f64(m, _cuda(x)).cpu().numpy()
+    yi_ref = op.inverse_mass_apply(x)
+    assert np.max(np.abs(yi - yi_ref)) <= 1e-12 * np.max(np.abs(yi_ref))
+
+
+def test_double_float_nonfinite_inputs_propagate():
+    """NaN and +-inf in the input give non-finite outputs in double-float,
+    exactly where native FP64 gives them (same data flow); the other outputs
+    keep the 1e-12 bar."""
+    from paper_1607_01323_gb300 import apply_inverse_mass_f64, apply_laplace_f64
+    c = channel((3, 4, 2))
+    k = 3
+    op = SIPG(oracle_spec(c), k)
+    m64 = gpu_mesh(c, k)
+    mdf = gpu_mesh(c, k)
+    mdf.set_f64_arithmetic("double_float")
+    N = m64.n_dofs
+    A = op.assemble()
+    norm_a = abs(A).sum(axis=1).max()
+    for bad in ([(5, np.nan)], [(200, np.inf)], [(7, -np.inf), (N - 3, np.nan)]):
+        x = uniform(N, "x")
+        for i, v in bad:
+            x[i] = v
+        for f in (apply_laplace_f64, apply_inverse_mass_f64):
+            y64 = f(m64, _cuda(x)).cpu().numpy()
+            ydf = f(mdf, _cuda(x)).cpu().numpy()
+            assert not np.all(np.isfinite(ydf))
+            np.testing.assert_array_equal(np.isfinite(ydf), np.isfinite(y64))
+            fin = np.isfinite(y64)
+            xf = np.where(np.isfinite(x), x, 0.0)
+            assert np.max(np.abs(ydf[fin] - y64[fin])) <= TOL64 * norm_a * np.max(np.abs(xf)) * 2
+
+
+def test_double_float_cg_nonfinite_initial_guess():
+    """A NaN in the initial guess of a double-float CG solve reaches the
+    residual (A x0 is NaN there) and the solve returns SIPG_NONFINITE."""
+    from paper_1607_01323_gb300 import cg_solve
+    from paper_1607_01323_gb300 import _lib as L
+    m = gpu_mesh(channel((3, 4, 2)), 3)
+    m.set_f64_arithmetic("double_float")
+    b = _cuda(uniform(m.n_dofs, "b"))
+    for bad in (float("nan"), float("inf")):
+        x0 = torch.zeros_like(b)
+        x0[11] = bad
+        _, r = cg_solve(m, b, x0, raise_on_fail=False)
+        assert r.status == L.NONFINITE
+    x, r = cg_solve(m, b)  # the context is still usable afterwards
+    assert r.converged
+
+
+def test_double_float_rejects_out_of_range_coefficients():
+    """Scalar coefficients outside [2^-100, 2^100] cannot be held in double-float
+    (FP32 exponents): the call is refused instead of computing a wrong result."""
+    from paper_1607_01323_gb300 import SipgError, apply_helmholtz_f64
+    m = gpu_mesh(channel((2, 2, 2)), 2)
+    m.set_f64_arithmetic("double_float")
+    x = _cuda(uniform(m.n_dofs, "x"))
+    for cm, nu in ((1e35, 1.0), (1.0, 1e-35), (1e-40, 1.0)):
+        with pytest.raises(SipgError):
+            apply_helmholtz_f64(m, x, cm, nu)
+    m.set_f64_arithmetic("native")
+    assert torch.all(torch.isfinite(apply_helmholtz_f64(m, x, 1e35, 1.0)))
+
+
+@pytest.mark.parametrize("arith", ["native", "double_float"])
 @pytest.mark.parametrize("cpb", [1, 3, 5, 7])
-def test_laplace_ragged_tiles(cpb):
+def test_laplace_ragged_tiles(cpb, arith):
     """Cells per block that do not divide the cell count leave a ragged last tile."""
     from paper_1607_01323_gb300 import apply_laplace_f32, apply_laplace_f64
     c = channel((3, 4, 3))
     k = 3
     op = SIPG(oracle_spec(c), k)
     m = gpu_mesh(c, k)
+    m.set_f64_arithmetic(arith)
     m.set_cells_per_block(0, cpb)
     m.set_cells_per_block(1, cpb)
     x = uniform(m.n_dofs, "x")
