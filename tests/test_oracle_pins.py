@@ -344,6 +344,49 @@ def test_adjoint_gradient_finite_differences():
         assert abs(fd - g[e]) <= 1e-6 * abs(g).max(), (e, fd, g[e])
 
 
+def _dA_dnu(op, nu, e, cm=1.0):
+    """dA/dnu_e of the assembled operator by a central difference (A is linear in
+    nu_e while the max of each face stays on the same side: exact to rounding)."""
+    h = 1e-3 * nu[e]
+    nup, num = nu.copy(), nu.copy()
+    nup[e] += h
+    num[e] -= h
+    return ((op.assemble(mass_coef=cm, nu_cell=nup) - op.assemble(mass_coef=cm, nu_cell=num)) / (2 * h)).toarray()
+
+
+def test_adjoint_term_magnitude_bounds():
+    """|lambda|^T |dA/dnu_e| |u| summed block by block bounds the gradient
+    (|-lambda^T dA/dnu_e u| <= it) and the entrywise absolute value of the
+    assembled derivative (|lambda|^T |dA/dnu_e| |u| <= it), both computed here
+    from the assembled matrix; it is homogeneous in lambda and u."""
+    spec = channel((2, 4, 2))
+    op = SIPG(spec, 2)
+    rng = np.random.default_rng(8)
+    nu = np.exp(0.5 * rng.standard_normal(spec.ncell))
+    u = rng.uniform(-1, 1, spec.ncell * op.P)
+    lam = rng.uniform(-1, 1, spec.ncell * op.P)
+    gm = adjoint.grad_nu_magnitude(op, nu, u, lam)
+    assert np.all(gm > 0)
+    assert np.allclose(adjoint.grad_nu_magnitude(op, nu, -3.0 * u, 0.5 * lam), 1.5 * gm, rtol=1e-14)
+    for e in range(spec.ncell):
+        dA = _dA_dnu(op, nu, e)
+        assert abs(lam @ dA @ u) <= gm[e] * (1 + 1e-9)
+        assert np.abs(lam) @ np.abs(dA) @ np.abs(u) <= gm[e] * (1 + 1e-9), e
+
+
+def test_adjoint_term_magnitude_single_neumann_cell():
+    """One cell with Neumann faces only: dA/dnu_e is the cell stiffness alone,
+    and the magnitude equals |lambda|^T |dA/dnu_e| |u| exactly."""
+    spec = MeshSpec(1, 1, 1, hi=(1.0, 0.8, 1.3), bc_lo=(N_,) * 3, bc_hi=(N_,) * 3)
+    op = SIPG(spec, 3)
+    rng = np.random.default_rng(9)
+    nu = np.array([0.7])
+    u, lam = rng.uniform(-1, 1, op.P), rng.uniform(-1, 1, op.P)
+    dA = _dA_dnu(op, nu, 0)
+    ref = np.abs(lam) @ np.abs(dA) @ np.abs(u)
+    assert abs(adjoint.grad_nu_magnitude(op, nu, u, lam)[0] - ref) <= 1e-9 * ref
+
+
 # ------------------------------------------------------------ mutations
 def test_mutation_average_weight_caught(monkeypatch):
     """Dropping the 1/2 of the average {{grad u}} breaks Galerkin consistency."""
