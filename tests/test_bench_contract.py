@@ -26,3 +26,4 @@ def test_reference_arm_json_line():
     import bench
     assert line["metric"] == bench.METRIC  # the same metric as the library's own line
     assert line["config"]["workload"].startswith("poisson_channel_32x32x32_k4")
+    assert line["config"] == bench.bench_config(1)  # the same config dict as the GPU arm's line
