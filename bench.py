@@ -580,6 +580,31 @@ def run_apply_only(args):
         print("apply %s n=%s k=%d dofs=%d: %.4f ms" % (args.precision, n, k, m.n_dofs, ev[0].elapsed_time(ev[1])))
 
 
+def run_solve_only(args):
+    """A few Jacobi-PCG solves of the bench problem (native or double-float FP64
+    operator, or --precond), timed with CUDA events; for ncu launch lists."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1607_01323_gb300 import Mesh, apply_mass_f64, cg_solve
+    w = dict(WORKLOAD)
+    n = (args.cells,) * 3 if args.cells else w["n"]
+    k = args.k if args.k else w["k"]
+    m = Mesh(n, w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=w["mapping"], gamma=w["gamma"], k=k)
+    m.set_f64_arithmetic(args.f64)
+    b = apply_mass_f64(m, torch.tensor(manufactured_f(m.node_coordinates()), device="cuda"))
+    x = torch.zeros_like(b)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for i in range(args.reps):
+        x.zero_()
+        ev[0].record()
+        _, r = cg_solve(m, b, x, precond=args.precond, rtol=RTOL, use_graph=1, check_every=CHECK_EVERY)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print("solve %s %s n=%s k=%d dofs=%d: %d iterations, %.3f ms" % (args.f64, args.precond, n, k, m.n_dofs,
+                                                                          r.iters, ev[0].elapsed_time(ev[1])))
+
+
 def run_convective_only(args):
     """A few convective-term applies on the bench channel (or --cells/--k)
     with a laminar profile plus noise, timed with CUDA events; for ncu captures."""
@@ -860,9 +885,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "vcycle", "convective"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "vcycle", "convective", "solve_only"],
                     help="apply: only operator applies; vcycle: only multigrid V-cycles; convective: only "
-                         "convective-term applies")
+                         "convective-term applies; solve_only: only CG solves of the bench problem")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "gmg_f32", "none", "invmass"],
+                    help="preconditioner of --mode solve_only")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--cells", type=int, default=0)
     ap.add_argument("--k", type=int, default=0)
@@ -879,6 +906,8 @@ def main():
         run_vcycle_only(args)
     elif args.mode == "convective":
         run_convective_only(args)
+    elif args.mode == "solve_only":
+        run_solve_only(args)
     elif args.workload != "c2":
         run_config(args)
     elif args.impl == "reference":
