@@ -68,7 +68,9 @@ struct LayerOff {
   static constexpr int RM = (P * P + 3) / 4 * 4, RV = (P + 3) / 4 * 4;  // padded block sizes (lmat, lvec)
   static constexpr int M = 0, K = RM, Mi = 2 * RM, Kc = 3 * RM, dL = 4 * RM, dR = 4 * RM + RV, dLh = 4 * RM + 2 * RV,
                        dRh = 4 * RM + 3 * RV, h = 4 * RM + 4 * RV, t = 4 * RM + 4 * RV + 1, ts = 4 * RM + 4 * RV + 2,
-                       dTL = 4 * RM + 4 * RV + 3, dTR = 4 * RM + 4 * RV + 4, stride = 4 * RM + 4 * RV + 8;
+                       dTL = 4 * RM + 4 * RV + 3, dTR = 4 * RM + 4 * RV + 4, Qc = 4 * RM + 4 * RV + 8,
+                       mL = 5 * RM + 4 * RV + 8, mR = 5 * RM + 5 * RV + 8, qL = 5 * RM + 6 * RV + 8,
+                       qR = 5 * RM + 7 * RV + 8, stride = 5 * RM + 8 * RV + 8;
 };
 
 // Neighbour across side (0 = low, 1 = high) of direction dir.  kind: 0 interior
@@ -605,15 +607,51 @@ __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* _
   }
 }
 
+// The uniform-viscosity line operator premultiplied by the layer's inverse 1D
+// mass: Mi (Kc u + face terms) = Qc u + sR mR + uR[0] qR + sL mL - uL[p-1] qL
+// with the precomputed Qc = Mi Kc, mL, mR = Mi e_0, Mi e_(p-1) (the columns
+// through which the end-value terms enter) and qL, qR = Mi dLh, Mi dRh (the
+// scatter of the neighbour's trace); sR, sL are the end-value terms of
+// line_op_u (penalty of the jump minus / plus the neighbour's half normal
+// derivative; 2 tau_e u on a Dirichlet face).
+template <typename T, int P>
+__device__ __forceinline__ void line_op_q(T (&w)[P], const T (&u)[P], const T* __restrict__ L, int kindL,
+                                          const T (&uL)[P], const T* __restrict__ LL, T tauFL, int kindR,
+                                          const T (&uR)[P], const T* __restrict__ LR, T tauFR, T tau2e) {
+  using O = LayerOff<P>;
+  matvec(w, L + O::Qc, u);
+  if (kindR == 0) {
+    const T gn = dotp(LR + O::dLh, uR);
+    axpy_vec(w, L + O::mR, fma(tauFR, u[P - 1] - uR[0], -gn));
+    axpy_vec(w, L + O::qR, uR[0]);
+  } else if (kindR == SIPG_BC_DIRICHLET) {
+    axpy_vec(w, L + O::mR, tau2e * u[P - 1]);
+  }
+  if (kindL == 0) {
+    const T gn = dotp(LL + O::dRh, uL);
+    axpy_vec(w, L + O::mL, fma(-tauFL, uL[P - 1] - u[0], gn));
+    axpy_vec(w, L + O::qL, -uL[P - 1]);
+  } else if (kindL == SIPG_BC_DIRICHLET) {
+    axpy_vec(w, L + O::mL, tau2e * u[0]);
+  }
+}
+
 // y = scale * (L x + mass_rel M x) for a uniform viscosity: scale = nu,
-// mass_rel = mass_coef / nu (Laplace: scale 1, mass_rel 0).  Same phases as
-// apply_kernel with the precombined line operator.
+// mass_rel = mass_coef / nu (Laplace: scale 1, mass_rel 0).  With the 1D
+// masses of the cell's layers, (I x My x Mz) = (Mx x My x Mz)(Mx^-1 x I x I)
+// and likewise for y and z, so
+//   y_e = (Mx x My x Mz) [ (Mx^-1 w_x) + (My^-1 w_y) + (Mz^-1 w_z) + mass_rel u ]
+// (each Md^-1 along its own direction): three line operators premultiplied by
+// the inverse mass (line_op_q) and three mass contractions instead of five.
+// Phases per cell (one line per thread): X (x-lines) -> V1, Y (y-lines) -> V2,
+// Z (z-lines): V1 + V2 + own line operator (+ mass_rel u), then Mz -> V1,
+// Y2: My -> V1, X2: Mx -> global.  The factorisation is exact; its rounding
+// grows by the row sums of |M||M^-1 Kc| against |Kc| (2.3x at p = 5).
 // Blocks per SM requested from the register allocator: the double-float
-// kernel fits 80 registers without spills up to p = 5, which allows three
-// 256-thread blocks (24 warps) per SM, and 128 (two blocks) up to p = 7; the
-// FP32 kernel fits 64 registers (four
-// blocks) up to p = 6; native FP64 keeps two blocks (128 registers) up to p = 6
-// so that enough warps feed the FP64 pipe.
+// kernel fits 80 registers up to p = 5, which allows three 256-thread blocks
+// (24 warps) per SM, and 128 (two blocks) up to p = 7; the FP32 kernel fits 64
+// registers (four blocks) up to p = 6; native FP64 keeps two blocks (128
+// registers) up to p = 6 so that enough warps feed the FP64 pipe.
 template <typename T, int P>
 struct UniformMinBlocks {
   static constexpr int value = std::is_same<T, dfl>::value ? (P <= 5 ? 3 : (P <= 7 ? 2 : 1))
@@ -621,19 +659,18 @@ struct UniformMinBlocks {
 };
 
 // Shared memory of apply_uniform_kernel: own cells (kept to the end for the
-// dot products and the Chebyshev epilogue) and three line-result buffers.
+// dot products and the Chebyshev epilogue) and two line-result buffers.
 template <typename T, int P>
 __host__ __device__ constexpr size_t uniform_smem_bytes(int cpb) {
-  return (size_t)4 * cpb * P * P * P * sizeof(T);
+  return (size_t)3 * cpb * P * P * P * sizeof(T);
 }
 
 // CHEB (FP32 only): instead of storing y = A x, apply one Chebyshev step of the
 // multigrid smoother to the block's own unknowns with x = d (see ChebEpi).
 template <typename T, typename S, int P, bool CHEB = false>
-__global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value) apply_uniform_kernel(Geo<T> g, const S* __restrict__ x,
-                                                                        S* __restrict__ y, int cpb, T mass_rel,
-                                                                        T scale, int do_scale, int do_mass,
-                                                                        DotSink sink, ChebEpi epi) {
+__global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value)
+    apply_uniform_kernel(Geo<T> g, const S* __restrict__ x, S* __restrict__ y, int cpb, T mass_rel, T scale,
+                         int do_scale, int do_mass, DotSink sink, ChebEpi epi) {
   if (sink.skip && *sink.skip) return;
   double* dots = sink.partials;
   using O = LayerOff<P>;
@@ -642,7 +679,6 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   T* su = reinterpret_cast<T*>(smem_raw);
   T* s1 = su + cpb * P3;
   T* s2 = s1 + cpb * P3;
-  T* s3 = s2 + cpb * P3;
   const int cs = threadIdx.x / P2;
   const int t = threadIdx.x - cs * P2;
   const int ti = t % P, tj = t / P;
@@ -659,9 +695,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   }
   __syncthreads();
   T* us = su + cs * P3;
-  T* w1 = s1 + cs * P3;
-  T* w2 = s2 + cs * P3;
-  T* w3 = s3 + cs * P3;
+  T* v1 = s1 + cs * P3;
+  T* v2 = s2 + cs * P3;
   int id[3] = {0, 0, 0};
   T tau_e = T(0);
   if (active) {
@@ -673,6 +708,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   }
   const T tau2e = tau_e + tau_e;
   if (active) {
+    // phases X and Y: Mx^-1 w_x on the x-lines -> V1, My^-1 w_y on the y-lines -> V2
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
       int start, step;
@@ -684,7 +720,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
       T u[P], uL[P], uR[P], w[P];
       load_line<T, P>(u, us, start, step);
       // a neighbour staged in this block is read from shared memory (read-only
-      // during phases X and Y), otherwise from global memory
+      // from here on), otherwise from global memory
       if (kL == 0) {
         const long long sl = (long long)nbL - cell0;
         if (sl >= 0 && sl < nc)
@@ -699,27 +735,17 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
         else
           load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
       }
-      line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
+      line_op_q<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
                       kR == 0 ? g.tab[dir] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
-      store_line<T, P>(dir == 0 ? w1 : w2, w, start, step);
+      store_line<T, P>(dir == 0 ? v1 : v2, w, start, step);
     }
   }
   __syncthreads();
   if (active) {
+    // phase Z on the z-lines: V1 + V2 + Mz^-1 w_z (+ mass_rel u), then Mz -> V1
     int start, step;
     line_geom<P>(2, ti, tj, start, step);
     const T* L = g.tab[2] + id[2] * O::stride;
-    // each contraction is finished and stored before the next starts (short
-    // live ranges, fewer registers); every thread touches only its own z-line
-    {
-      T v[P], r[P];
-      load_line<T, P>(v, w1, start, step);
-      matvec(r, L + O::M, v);
-      store_line<T, P>(w1, r, start, step);
-      load_line<T, P>(v, w2, start, step);
-      matvec(r, L + O::M, v);
-      store_line<T, P>(w2, r, start, step);
-    }
     int nbL, nbR, kL, kR, jl, jr;
     face_neighbor(g, 2, 0, id[2], e, nbL, kL, jl);
     face_neighbor(g, 2, 1, id[2], e, nbR, kR, jr);
@@ -727,42 +753,44 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     load_line<T, P>(u, us, start, step);
     if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step, sc);
     if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
-    line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
+    line_op_q<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
                     kR == 0 ? g.tab[2] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
     if (do_mass) {
-      T mu[P];
-      matvec(mu, L + O::M, u);
 #pragma unroll
-      for (int a = 0; a < P; ++a) w[a] = fma(mass_rel, mu[a], w[a]);
+      for (int a = 0; a < P; ++a) w[a] = fma(mass_rel, u[a], w[a]);
     }
-    store_line<T, P>(w3, w, start, step);
+    {
+      T v[P];
+      load_line<T, P>(v, v1, start, step);
+#pragma unroll
+      for (int a = 0; a < P; ++a) w[a] += v[a];
+      load_line<T, P>(v, v2, start, step);
+#pragma unroll
+      for (int a = 0; a < P; ++a) w[a] += v[a];
+    }
+    T r[P];
+    matvec(r, L + O::M, w);
+    store_line<T, P>(v1, r, start, step);
   }
   __syncthreads();
   if (active) {
+    // phase Y2 on the y-lines: My -> V1
     int start, step;
     line_geom<P>(1, ti, tj, start, step);
-    const T* My = g.tab[1] + id[1] * O::stride + O::M;
     T v[P], r[P];
-    load_line<T, P>(v, w1, start, step);
-    matvec(r, My, v);
-    store_line<T, P>(w1, r, start, step);
-    load_line<T, P>(v, w3, start, step);
-    matvec(r, My, v);
-    load_line<T, P>(v, w2, start, step);
-#pragma unroll
-    for (int a = 0; a < P; ++a) r[a] += v[a];
-    store_line<T, P>(w2, r, start, step);
+    load_line<T, P>(v, v1, start, step);
+    matvec(r, g.tab[1] + id[1] * O::stride + O::M, v);
+    store_line<T, P>(v1, r, start, step);
   }
   __syncthreads();
   double d_xy = 0.0, d_y = 0.0, d_x = 0.0;
   if (active) {
+    // phase X2 on the x-lines: Mx -> global (or the Chebyshev step)
     int start, step;
     line_geom<P>(0, ti, tj, start, step);
-    const T* Mx = g.tab[0] + id[0] * O::stride + O::M;
-    T v[P], out[P], r1[P];
-    load_line<T, P>(v, w2, start, step);
-    matvec(out, Mx, v);
-    load_line<T, P>(r1, w1, start, step);
+    T v[P], out[P];
+    load_line<T, P>(v, v1, start, step);
+    matvec(out, g.tab[0] + id[0] * O::stride + O::M, v);
     if constexpr (CHEB) {
       static_assert(std::is_same<T, float>::value && std::is_same<S, float>::value, "FP32 only");
       // t = A d for this x-line; d (the input) from the staged cell
@@ -771,7 +799,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
       const long long o = cbase + (long long)e * P3 + start;
 #pragma unroll
       for (int a = 0; a < P; ++a) {
-        T tt = out[a] + r1[a];
+        T tt = out[a];
         if (do_scale) tt *= scale;
         const float ri = epi.r[o + a] - tt;
         const float di = epi.c1 * dold[a] + epi.c2 * ri * epi.dinv[o + a];
@@ -783,7 +811,6 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
       S* yo = y + cbase + (long long)e * P3 + start;
 #pragma unroll
       for (int a = 0; a < P; ++a) {
-        out[a] += r1[a];
         if (do_scale) out[a] *= scale;
         yo[a] = cvt_out<S, T>(out[a], sc);
       }

@@ -34,14 +34,19 @@ constexpr int kMaxCellThreads = 256;  // block size limit of the cell kernels (r
 //   ts  = f (k+1)^2 t (this layer's share of tau_e),
 //   dTL, dTR = max(0, ts of the low / high neighbour layer - ts), so that the
 //   face penalty max(tau_e, tau_neighbour) of Eq. (tau) is tau_e + dT.
+// The uniform-viscosity kernel evaluates the cell operator as
+// (Mx x My x Mz) sum_d (M_d^-1 along d) w_d, so it also keeps the line operator
+// premultiplied by the inverse mass:
+//   Qc = Mi Kc,  mL = Mi e_0, mR = Mi e_(p-1),  qL = Mi dLh, qR = Mi dRh.
 // Table layout per layer, stride lstride(p); every matrix block is padded to
 // lmat(p) = p*p rounded up to a multiple of 4 entries and every vector block to
 // lvec(p) = p rounded up to 4, so that each block starts 16-byte aligned (FP32
 // kernels read the blocks with 128-bit loads):
 //   [M][K][Mi][Kc] (lmat each) [dL][dR][dLh][dRh] (lvec each) [h][t][ts][dTL][dTR][0][0][0]
+//   [Qc] (lmat) [mL][mR][qL][qR] (lvec each)
 inline int lmat(int p) { return (p * p + 3) / 4 * 4; }
 inline int lvec(int p) { return (p + 3) / 4 * 4; }
-inline int lstride(int p) { return 4 * lmat(p) + 4 * lvec(p) + 8; }
+inline int lstride(int p) { return 5 * lmat(p) + 8 * lvec(p) + 8; }
 inline int lay_M(int) { return 0; }
 inline int lay_K(int p) { return lmat(p); }
 inline int lay_Mi(int p) { return 2 * lmat(p); }
@@ -55,6 +60,11 @@ inline int lay_t(int p) { return 4 * lmat(p) + 4 * lvec(p) + 1; }
 inline int lay_ts(int p) { return 4 * lmat(p) + 4 * lvec(p) + 2; }
 inline int lay_dTL(int p) { return 4 * lmat(p) + 4 * lvec(p) + 3; }
 inline int lay_dTR(int p) { return 4 * lmat(p) + 4 * lvec(p) + 4; }
+inline int lay_Qc(int p) { return 4 * lmat(p) + 4 * lvec(p) + 8; }
+inline int lay_mL(int p) { return 5 * lmat(p) + 4 * lvec(p) + 8; }
+inline int lay_mR(int p) { return 5 * lmat(p) + 5 * lvec(p) + 8; }
+inline int lay_qL(int p) { return 5 * lmat(p) + 6 * lvec(p) + 8; }
+inline int lay_qR(int p) { return 5 * lmat(p) + 7 * lvec(p) + 8; }
 
 // Geometry arguments shared by all cell kernels (passed by value).
 template <typename T>

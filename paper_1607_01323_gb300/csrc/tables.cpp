@@ -277,6 +277,23 @@ int build_tables(Mesh& m) {
         L[lay_dLh(p) + a] = 0.5 * dL[a];
         L[lay_dRh(p) + a] = 0.5 * dR[a];
       }
+      // the line operator premultiplied by the inverse mass (extended precision)
+      for (int a = 0; a < p; ++a) {
+        long double q = 0.0L, ql = 0.0L, qr = 0.0L;
+        for (int b = 0; b < p; ++b) {
+          ql += Mi[a * p + b] * (long double)L[lay_dLh(p) + b];
+          qr += Mi[a * p + b] * (long double)L[lay_dRh(p) + b];
+        }
+        for (int c = 0; c < p; ++c) {
+          q = 0.0L;
+          for (int b = 0; b < p; ++b) q += Mi[a * p + b] * (long double)L[lay_Kc(p) + b * p + c];
+          L[lay_Qc(p) + a * p + c] = (double)q;
+        }
+        L[lay_mL(p) + a] = (double)Mi[a * p];
+        L[lay_mR(p) + a] = (double)Mi[a * p + p - 1];
+        L[lay_qL(p) + a] = (double)ql;
+        L[lay_qR(p) + a] = (double)qr;
+      }
     }
     // penalty shares and face increments (Eq. (taue), Eq. (tau))
     const double s = m.penalty * (m.k + 1) * (m.k + 1);
