@@ -683,7 +683,8 @@ def run_config(args):
     v3c: divergence, gradient, tau_D and the div-div local projection of the
         pressure-projection step on the 32^3 k=4 channel;
     ns: the dual-splitting time step (BDF3, V3c) on the 32^3 k=4 channel;
-    perturbed: the general-metric FP64 apply on a 32^3 perturbed box, k=4."""
+    perturbed: the general-metric FP64 apply on a 32^3 perturbed box, k=4;
+    mg_scaling: multigrid and Jacobi PCG iteration counts on refined channels."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -845,6 +846,23 @@ def run_config(args):
                                     "ms": 1e3 * t, "dofs_per_s": N / t,
                                     "algorithmic_bytes_per_dof": 16 + geo_bytes,
                                     "achieved_gbs": N * (16 + geo_bytes) / t / 1e9}
+    elif args.workload == "mg_scaling":
+        # iteration counts of FP32-multigrid PCG (Sec. 5.1) and Jacobi PCG to
+        # 1e-10 on refined channels: graded (tanh, gamma 1.8 / 0.9 / 0.3),
+        # straight cells on the graded vertices, and the uniform box, k = 4,
+        # seeded uniform rhs
+        from paper_1607_01323_gb300 import Mesh as M_
+        rows = []
+        for mapping, gamma in (("channel", 1.8), ("channel_linear", 1.8), ("channel", 0.9), ("channel", 0.3),
+                               ("affine", 1.8)):
+            for n in (8, 16, 32):
+                m = M_((n, n, n), w["lo"], w["hi"], w["bc_lo"], w["bc_hi"], mapping=mapping, gamma=gamma, k=4)
+                b = torch.tensor(inputs.uniform(0, "b", m.n_dofs), device="cuda")
+                _, rg = cg_solve(m, b, precond="gmg_f32", rtol=1e-10)
+                _, rj = cg_solve(m, b, precond="jacobi", rtol=1e-10, maxit=20000)
+                rows.append({"mapping": mapping, "gamma": gamma, "n": n, "gmg_iters": rg.iters,
+                             "jacobi_iters": rj.iters})
+        out["mg_scaling_k4"] = rows
     elif args.workload == "v3c":
         # the pressure-projection neighbours of the Poisson solve (variant V3c)
         # on the 32^3 k=4 channel: divergence rhs, pressure gradient, tau_D
@@ -897,7 +915,8 @@ def main():
     ap.add_argument("--f64", default="native", choices=["native", "double_float"],
                     help="arithmetic of the FP64 operator of the timed solves (native FP64, the default, or "
                          "double_float: FP32 pairs on the FP32 pipes)")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "v3c", "ns", "perturbed"],
+    ap.add_argument("--workload", default="c2",
+                    choices=["c1", "c2", "c3", "c4", "c5", "v3c", "ns", "perturbed", "mg_scaling"],
                     help="c2 (default) is the bench step; c1, c3-c5, v3c, ns print timings of other workloads")
     args = ap.parse_args()
     if args.mode == "apply":
