@@ -459,10 +459,14 @@ int sipg_adjoint_grad_nu(const sipg_mesh* mesh, const double* nu_cell, const dou
                          double* grad, void* stream);
 
 /* Choose the cells-per-block of the operator kernels for this mesh and
- * precision (0 = FP64, 1 = FP32) by timing the candidates with CUDA events.
- * If cache_path is not NULL the choice is read from / appended to that text
- * file (one "key value" line per (k, precision, map, mesh size)).  precision
- * 2 tunes the convective kernel for the mesh's current FP64 arithmetic. */
+ * precision (0 = FP64, 1 = FP32, also choosing the FP32 thread mapping) by
+ * timing the candidates with CUDA events.  If cache_path is not NULL the
+ * choice is read from / stored in that JSON file, an object with one entry
+ * "k=<k> prec=<precision> map=<map> n=<nx>x<ny>x<nz>[ arith=native|df]":
+ * {"cpb": <cells per block>, "mapping": <sipg_threads>} per configuration
+ * (the file is rewritten whole on every store; a file of another shape counts
+ * as empty).  precision 2 tunes the convective kernel; the FP64 keys include
+ * the mesh's current FP64 arithmetic. */
 int sipg_autotune(sipg_mesh* mesh, int precision, const char* cache_path);
 
 /* Arithmetic of the FP64 operator entry points (sipg_apply_laplace_f64,

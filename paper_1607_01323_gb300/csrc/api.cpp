@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <map>
 #include <sstream>
 #include <string>
 #include <type_traits>
@@ -720,6 +721,62 @@ int sipg_set_cells_per_block(sipg_mesh* m, int precision, int cpb) {
   return SIPG_OK;
 }
 
+// Autotuner cache: a JSON object of entries
+//   "<key>": {"cpb": <cells per block>, "mapping": <FP32 thread mapping>}
+// Only files of this shape are read (written by cache_store); anything else
+// counts as an empty cache and is replaced on the next store.
+static std::map<std::string, std::pair<int, int>> cache_read(const char* path) {
+  std::map<std::string, std::pair<int, int>> out;
+  std::ifstream f(path);
+  if (!f) return out;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string s = ss.str();
+  size_t pos = s.find('{');
+  if (pos == std::string::npos) return out;
+  ++pos;
+  auto int_after = [&](size_t from, size_t to, const char* name, int* v) {
+    const size_t k = s.find(name, from);
+    if (k == std::string::npos || k > to) return false;
+    const size_t c = s.find(':', k);
+    if (c == std::string::npos || c > to) return false;
+    *v = std::atoi(s.c_str() + c + 1);
+    return true;
+  };
+  while (true) {
+    const size_t q0 = s.find('"', pos);
+    if (q0 == std::string::npos) break;
+    const size_t q1 = s.find('"', q0 + 1);
+    const size_t o0 = q1 == std::string::npos ? q1 : s.find('{', q1);
+    const size_t o1 = o0 == std::string::npos ? o0 : s.find('}', o0);
+    if (o1 == std::string::npos) break;
+    int cpb = 0, mapping = 0;
+    if (int_after(o0, o1, "\"cpb\"", &cpb) && cpb > 0) {
+      int_after(o0, o1, "\"mapping\"", &mapping);
+      out[s.substr(q0 + 1, q1 - q0 - 1)] = {cpb, mapping};
+    }
+    pos = o1 + 1;
+  }
+  return out;
+}
+
+static void cache_store(const char* path, const std::string& key, int cpb, int mapping) {
+  auto entries = cache_read(path);
+  entries[key] = {cpb, mapping};
+  const std::string tmp = std::string(path) + ".tmp";
+  {
+    std::ofstream f(tmp, std::ios::trunc);
+    if (!f) return;
+    f << "{\n";
+    size_t i = 0;
+    for (const auto& kv : entries)
+      f << "  \"" << kv.first << "\": {\"cpb\": " << kv.second.first << ", \"mapping\": " << kv.second.second
+        << "}" << (++i < entries.size() ? "," : "") << "\n";
+    f << "}\n";
+  }
+  std::rename(tmp.c_str(), path);  // whole-file replacement (no partial file is ever read)
+}
+
 // Cells per block of the convective kernel: every feasible count, timed on a
 // zero velocity field (the kernel's work does not depend on the values).
 static int autotune_convective(sipg_mesh* m, int* best_out) {
@@ -779,25 +836,22 @@ int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
   char key[160];
   std::snprintf(key, sizeof(key), "k=%d prec=%d map=%d n=%dx%dx%d%s", m->k, precision, m->desc.map, m->desc.n[0],
                 m->desc.n[1], m->desc.n[2],
-                precision == 2 ? (m->f64_arith == SIPG_F64_DOUBLE_FLOAT ? " arith=df" : " arith=native") : "");
+                precision != 1 ? (m->f64_arith == SIPG_F64_DOUBLE_FLOAT ? " arith=df" : " arith=native") : "");
   if (cache_path) {
-    std::ifstream f(cache_path);
-    std::string line;
-    while (std::getline(f, line)) {
-      const size_t bar = line.rfind(" cpb=");
-      if (bar != std::string::npos && line.substr(0, bar) == key) {
-        const int c = std::atoi(line.c_str() + bar + 5);
-        if (sipg_set_cells_per_block(m, precision, c) == SIPG_OK) return SIPG_OK;
-      }
+    const auto entries = cache_read(cache_path);
+    const auto it = entries.find(key);
+    if (it != entries.end()) {
+      const int old_map = m->f32_mapping;
+      if (precision == 1 && (it->second.second == SIPG_THREADS_LINE || it->second.second == SIPG_THREADS_PLANE))
+        m->f32_mapping = it->second.second;
+      if (sipg_set_cells_per_block(m, precision, it->second.first) == SIPG_OK) return SIPG_OK;
+      m->f32_mapping = old_map;
     }
   }
   if (precision == 2) {
     int best = 0;
     if ((st = autotune_convective(m, &best))) return st;
-    if (cache_path) {
-      std::ofstream f(cache_path, std::ios::app);
-      if (f) f << key << " cpb=" << best << "\n";
-    }
+    if (cache_path) cache_store(cache_path, key, best, 0);
     return SIPG_OK;
   }
   if ((st = set_device(*m))) return st;
@@ -862,10 +916,7 @@ int sipg_autotune(sipg_mesh* m, int precision, const char* cache_path) {
     return fail(SIPG_ECUDA, "autotune: no candidate ran");
   }
   m->cpb[precision] = best;
-  if (cache_path) {
-    std::ofstream f(cache_path, std::ios::app);
-    if (f) f << key << " cpb=" << best << "\n";
-  }
+  if (cache_path) cache_store(cache_path, key, best, precision == 1 ? m->f32_mapping : 0);
   return SIPG_OK;
 }
 

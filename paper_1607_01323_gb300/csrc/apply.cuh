@@ -70,7 +70,8 @@ struct LayerOff {
                        dRh = 4 * RM + 3 * RV, h = 4 * RM + 4 * RV, t = 4 * RM + 4 * RV + 1, ts = 4 * RM + 4 * RV + 2,
                        dTL = 4 * RM + 4 * RV + 3, dTR = 4 * RM + 4 * RV + 4, Qc = 4 * RM + 4 * RV + 8,
                        mL = 5 * RM + 4 * RV + 8, mR = 5 * RM + 5 * RV + 8, qL = 5 * RM + 6 * RV + 8,
-                       qR = 5 * RM + 7 * RV + 8, stride = 5 * RM + 8 * RV + 8;
+                       qR = 5 * RM + 7 * RV + 8, cs = 4 * RM + 4 * RV + 5, EQc = 5 * RM + 8 * RV + 8,
+                       EKc = 6 * RM + 8 * RV + 8, EM = 7 * RM + 8 * RV + 8, stride = 8 * RM + 8 * RV + 8;
 };
 
 // Neighbour across side (0 = low, 1 = high) of direction dir.  kind: 0 interior
@@ -243,6 +244,57 @@ __device__ __forceinline__ float dotp(const float* __restrict__ a, const float (
       if (4 * q + j < P) s = fmaf(e[j], v[4 * q + j], s);
   }
   return s;
+}
+
+// sum_b a[b] v[b] with scalar loads of a (no alignment assumed)
+template <typename T, int N>
+__device__ __forceinline__ T dot_s(const T* __restrict__ a, const T (&v)[N]) {
+  if constexpr (std::is_same<T, dfl>::value) {
+    return df_dot<N>(a, v);
+  } else {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < N; ++b) s = fma(a[b], v[b], s);
+    return s;
+  }
+}
+
+// out = A v for a centrosymmetric A in the even-odd form packed by the table
+// builder (E: h x (h + odd), O: h x h, Z: h + 1 for odd p; h = p / 2): with
+// e_b = v_b + v_(p-1-b), o_b = v_b - v_(p-1-b), s_a = E_a . (e, v_h) and
+// d_a = O_a . o, out_a = s_a + d_a, out_(p-1-a) = s_a - d_a, out_h = Z . (e, v_h).
+template <typename T, int P>
+__device__ __forceinline__ void matvec_eo(T (&out)[P], const T* __restrict__ E, const T (&v)[P]) {
+  constexpr int H = P / 2, OD = P & 1, EW = H + OD;
+  const T* __restrict__ Oo = E + H * EW;
+  T ev[EW], o[H];
+#pragma unroll
+  for (int b = 0; b < H; ++b) {
+    ev[b] = v[b] + v[P - 1 - b];
+    o[b] = v[b] - v[P - 1 - b];
+  }
+  if constexpr (OD) ev[H] = v[H];
+#pragma unroll
+  for (int a = 0; a < H; ++a) {
+    const T s = dot_s<T, EW>(E + a * EW, ev), d = dot_s<T, H>(Oo + a * H, o);
+    out[a] = s + d;
+    out[P - 1 - a] = s - d;
+  }
+  if constexpr (OD) out[H] = dot_s<T, EW>(Oo + H * H, ev);
+}
+
+// out = A v with the layer's matrix at offset `plain`, or its even-odd form at
+// offset `eo_off` when the layer is centrosymmetric (p >= 5)
+template <typename T, int P>
+__device__ __forceinline__ void matvec_l(T (&out)[P], const T* __restrict__ L, int plain, int eo_off, bool eo,
+                                         const T (&v)[P]) {
+  if constexpr (P >= 5) {
+    if (eo) {
+      matvec_eo<T, P>(out, L + eo_off, v);
+      return;
+    }
+  }
+  matvec(out, L + plain, v);
 }
 
 // w += c * (table vector block d): FP32 reads the block with 128-bit loads,
@@ -586,9 +638,10 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
 template <typename T, int P>
 __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* __restrict__ L, int kindL,
                                           const T (&uL)[P], const T* __restrict__ LL, T tauFL, int kindR,
-                                          const T (&uR)[P], const T* __restrict__ LR, T tauFR, T tau2e) {
+                                          const T (&uR)[P], const T* __restrict__ LR, T tauFR, T tau2e,
+                                          bool eo = false) {
   using O = LayerOff<P>;
-  matvec(w, L + O::Kc, u);
+  matvec_l<T, P>(w, L, O::Kc, O::EKc, eo, u);
   if (kindR == 0) {
     const T gn = dotp(LR + O::dLh, uR);
     const T J = u[P - 1] - uR[0];
@@ -617,9 +670,10 @@ __device__ __forceinline__ void line_op_u(T (&w)[P], const T (&u)[P], const T* _
 template <typename T, int P>
 __device__ __forceinline__ void line_op_q(T (&w)[P], const T (&u)[P], const T* __restrict__ L, int kindL,
                                           const T (&uL)[P], const T* __restrict__ LL, T tauFL, int kindR,
-                                          const T (&uR)[P], const T* __restrict__ LR, T tauFR, T tau2e) {
+                                          const T (&uR)[P], const T* __restrict__ LR, T tauFR, T tau2e,
+                                          bool eo) {
   using O = LayerOff<P>;
-  matvec(w, L + O::Qc, u);
+  matvec_l<T, P>(w, L, O::Qc, O::EQc, eo, u);
   if (kindR == 0) {
     const T gn = dotp(LR + O::dLh, uR);
     axpy_vec(w, L + O::mR, fma(tauFR, u[P - 1] - uR[0], -gn));
@@ -638,15 +692,17 @@ __device__ __forceinline__ void line_op_q(T (&w)[P], const T (&u)[P], const T* _
 
 // y = scale * (L x + mass_rel M x) for a uniform viscosity: scale = nu,
 // mass_rel = mass_coef / nu (Laplace: scale 1, mass_rel 0).  With the 1D
-// masses of the cell's layers, (I x My x Mz) = (Mx x My x Mz)(Mx^-1 x I x I)
-// and likewise for y and z, so
-//   y_e = (Mx x My x Mz) [ (Mx^-1 w_x) + (My^-1 w_y) + (Mz^-1 w_z) + mass_rel u ]
-// (each Md^-1 along its own direction): three line operators premultiplied by
-// the inverse mass (line_op_q) and three mass contractions instead of five.
-// Phases per cell (one line per thread): X (x-lines) -> V1, Y (y-lines) -> V2,
-// Z (z-lines): V1 + V2 + own line operator (+ mass_rel u), then Mz -> V1,
-// Y2: My -> V1, X2: Mx -> global.  The factorisation is exact; its rounding
-// grows by the row sums of |M||M^-1 Kc| against |Kc| (2.3x at p = 5).
+// masses of the cell's layers, (I x My x Mz) = (Mx x My x I)(Mx^-1 x I x Mz)
+// and (Mx x I x Mz) = (Mx x My x I)(I x My^-1 x Mz), so
+//   y_e = (Mx x My x I) [ Mz ((Mx^-1 w_x) + (My^-1 w_y) + mass_rel u) + w_z ]
+// (each Md^-1, Md along its own direction): the x and y line operators
+// premultiplied by the inverse mass (line_op_q), the z line operator plain
+// (line_op_u), and three mass contractions instead of five.  Phases per cell
+// (one line per thread): X (x-lines) -> V1, Y (y-lines) -> V2, Z (z-lines):
+// Mz (V1 + V2 + mass_rel u) + w_z -> V1, Y2: My -> V1, X2: Mx -> global.  The
+// factorisation is exact; its rounding grows by the row sums of
+// |M||M^-1 Kc| against |Kc| (2.3x at p = 5).  On centrosymmetric layers
+// (p >= 5) the contractions with Qc, Kc and M take the even-odd form.
 // Blocks per SM requested from the register allocator: the double-float
 // kernel fits 80 registers up to p = 5, which allows three 256-thread blocks
 // (24 warps) per SM, and 128 (two blocks) up to p = 7; the FP32 kernel fits 64
@@ -667,7 +723,9 @@ __host__ __device__ constexpr size_t uniform_smem_bytes(int cpb) {
 
 // CHEB (FP32 only): instead of storing y = A x, apply one Chebyshev step of the
 // multigrid smoother to the block's own unknowns with x = d (see ChebEpi).
-template <typename T, typename S, int P, bool CHEB = false>
+// EOXZ: every x- and z-layer of the mesh is centrosymmetric (Mesh::eo_xz):
+// their contractions take the even-odd form (p >= 5).
+template <typename T, typename S, int P, bool CHEB = false, bool EOXZ = false>
 __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value)
     apply_uniform_kernel(Geo<T> g, const S* __restrict__ x, S* __restrict__ y, int cpb, T mass_rel, T scale,
                          int do_scale, int do_mass, DotSink sink, ChebEpi epi) {
@@ -675,6 +733,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   double* dots = sink.partials;
   using O = LayerOff<P>;
   constexpr int P2 = P * P, P3 = P * P * P;
+  constexpr bool EOX = EOXZ && P >= 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* su = reinterpret_cast<T*>(smem_raw);
   T* s1 = su + cpb * P3;
@@ -736,16 +795,17 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
           load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
       }
       line_op_q<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
-                      kR == 0 ? g.tab[dir] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
+                      kR == 0 ? g.tab[dir] + jr * O::stride : L, tau_e + L[O::dTR], tau2e, dir == 0 && EOX);
       store_line<T, P>(dir == 0 ? v1 : v2, w, start, step);
     }
   }
   __syncthreads();
   if (active) {
-    // phase Z on the z-lines: V1 + V2 + Mz^-1 w_z (+ mass_rel u), then Mz -> V1
+    // phase Z on the z-lines: Mz (V1 + V2 + mass_rel u) + w_z -> V1
     int start, step;
     line_geom<P>(2, ti, tj, start, step);
     const T* L = g.tab[2] + id[2] * O::stride;
+    constexpr bool eoz = EOX;
     int nbL, nbR, kL, kR, jl, jr;
     face_neighbor(g, 2, 0, id[2], e, nbL, kL, jl);
     face_neighbor(g, 2, 1, id[2], e, nbR, kR, jr);
@@ -753,23 +813,23 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     load_line<T, P>(u, us, start, step);
     if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step, sc);
     if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
-    line_op_q<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
-                    kR == 0 ? g.tab[2] + jr * O::stride : L, tau_e + L[O::dTR], tau2e);
+    line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
+                    kR == 0 ? g.tab[2] + jr * O::stride : L, tau_e + L[O::dTR], tau2e, eoz);
+    T v[P], r[P];
+    load_line<T, P>(v, v1, start, step);
+    {
+      T v2l[P];
+      load_line<T, P>(v2l, v2, start, step);
+#pragma unroll
+      for (int a = 0; a < P; ++a) v[a] += v2l[a];
+    }
     if (do_mass) {
 #pragma unroll
-      for (int a = 0; a < P; ++a) w[a] = fma(mass_rel, u[a], w[a]);
+      for (int a = 0; a < P; ++a) v[a] = fma(mass_rel, u[a], v[a]);
     }
-    {
-      T v[P];
-      load_line<T, P>(v, v1, start, step);
+    matvec_l<T, P>(r, L, O::M, O::EM, eoz, v);
 #pragma unroll
-      for (int a = 0; a < P; ++a) w[a] += v[a];
-      load_line<T, P>(v, v2, start, step);
-#pragma unroll
-      for (int a = 0; a < P; ++a) w[a] += v[a];
-    }
-    T r[P];
-    matvec(r, L + O::M, w);
+    for (int a = 0; a < P; ++a) r[a] += w[a];
     store_line<T, P>(v1, r, start, step);
   }
   __syncthreads();
@@ -779,7 +839,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     line_geom<P>(1, ti, tj, start, step);
     T v[P], r[P];
     load_line<T, P>(v, v1, start, step);
-    matvec(r, g.tab[1] + id[1] * O::stride + O::M, v);
+    const T* Ly = g.tab[1] + id[1] * O::stride;
+    matvec_l<T, P>(r, Ly, O::M, O::EM, false, v);
     store_line<T, P>(v1, r, start, step);
   }
   __syncthreads();
@@ -790,7 +851,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     line_geom<P>(0, ti, tj, start, step);
     T v[P], out[P];
     load_line<T, P>(v, v1, start, step);
-    matvec(out, g.tab[0] + id[0] * O::stride + O::M, v);
+    const T* Lx = g.tab[0] + id[0] * O::stride;
+    matvec_l<T, P>(out, Lx, O::M, O::EM, EOX, v);
     if constexpr (CHEB) {
       static_assert(std::is_same<T, float>::value && std::is_same<S, float>::value, "FP32 only");
       // t = A d for this x-line; d (the input) from the staged cell

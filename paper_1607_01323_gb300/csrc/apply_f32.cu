@@ -18,18 +18,12 @@ static int launch_cheb_step_p(const Mesh& m, const float* d, const ChebEpi& epi,
   const int threads = (cpb * P * P + 31) / 32 * 32;
   const size_t smem = uniform_smem_bytes<float, P>(cpb);
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
-  if (smem + 2048 > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(apply_uniform_kernel<float, float, P, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply, Chebyshev step)");
-  }
   DotSink ds;
   ds.skip = skip;
   ds.sums = 0;
-  apply_uniform_kernel<float, float, P, true><<<grid, threads, smem, s>>>(make_geo<float>(m), d, nullptr, cpb, 0.f,
-                                                                          1.f, 0, 0, ds, epi);
+  const cudaError_t e = launch_uniform<float, float, P, true>(m, grid, threads, smem, s, make_geo<float>(m), d,
+                                                              (float*)nullptr, cpb, 0.f, 1.f, 0, 0, ds, epi);
   const_cast<Mesh&>(m).launches++;
-  cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch (Chebyshev step)");
 }
 

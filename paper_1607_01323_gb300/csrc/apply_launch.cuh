@@ -8,6 +8,24 @@
 
 namespace sipg {
 
+// Launch of apply_uniform_kernel, with the even-odd x/z contractions when the
+// mesh allows them (p >= 5, Mesh::eo_xz).
+template <typename T, typename S, int P, bool CHEB>
+static cudaError_t launch_uniform(const Mesh& m, dim3 grid, int threads, size_t smem, cudaStream_t s, const Geo<T>& g,
+                                  const S* x, S* y, int cpb, T mass_rel, T scale, int do_scale, int do_mass,
+                                  const DotSink& ds, const ChebEpi& epi) {
+  auto k = apply_uniform_kernel<T, S, P, CHEB, false>;
+  if constexpr (P >= 5) {
+    if (m.eo_xz) k = apply_uniform_kernel<T, S, P, CHEB, true>;
+  }
+  if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k<<<grid, threads, smem, s>>>(g, x, y, cpb, mass_rel, scale, do_scale, do_mass, ds, epi);
+  return cudaGetLastError();
+}
+
 template <typename T, int P>
 static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu, const T* nu_cell, bool stiff,
                           const DotSink* sink, int* nblocks, cudaStream_t s) {
@@ -42,11 +60,9 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
   const size_t smem = uniform ? uniform_smem_bytes<T, P>(cpb) : (size_t)3 * cpb * P * P * P * sizeof(T);
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
   const DotSink ds = sink ? *sink : DotSink();
-  if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
-    cudaError_t e = uniform ? cudaFuncSetAttribute(apply_uniform_kernel<T, T, P>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                            : cudaFuncSetAttribute(apply_kernel<T, T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)smem);
+  if (!uniform && smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel<T, T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
   }
   if (uniform) {
@@ -61,21 +77,19 @@ static int launch_apply_p(const Mesh& m, const T* x, T* y, int ncomp, T cm, T nu
           if (st) return st;
         }
         const Geo<dfl> gd = make_geo<dfl>(m);
-        if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
-          cudaError_t e = cudaFuncSetAttribute(apply_uniform_kernel<dfl, double, P>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-          if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply)");
-        }
-        apply_uniform_kernel<dfl, double, P><<<grid, threads, smem, s>>>(gd, x, y, cpb, dfl(cm / nu), dfl(nu),
-                                                                         do_scale, do_mass, ds, ChebEpi());
+        const cudaError_t e = launch_uniform<dfl, double, P, false>(m, grid, threads, smem, s, gd, x, y, cpb,
+                                                                    dfl(cm / nu), dfl(nu), do_scale, do_mass, ds,
+                                                                    ChebEpi());
         if (nblocks) *nblocks = (int)(grid.x * grid.y);
         const_cast<Mesh&>(m).launches++;
-        cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch");
       }
     }
-    apply_uniform_kernel<T, T, P><<<grid, threads, smem, s>>>(g, x, y, cpb, cm / nu, nu, do_scale, do_mass, ds,
-                                                              ChebEpi());
+    const cudaError_t e = launch_uniform<T, T, P, false>(m, grid, threads, smem, s, g, x, y, cpb, cm / nu, nu,
+                                                         do_scale, do_mass, ds, ChebEpi());
+    if (nblocks) *nblocks = (int)(grid.x * grid.y);
+    const_cast<Mesh&>(m).launches++;
+    return e == cudaSuccess ? SIPG_OK : cuda_fail(e, "apply kernel launch");
   } else {
     if constexpr (std::is_same<T, double>::value) {
       if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {

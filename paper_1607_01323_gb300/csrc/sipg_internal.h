@@ -42,11 +42,16 @@ constexpr int kMaxCellThreads = 256;  // block size limit of the cell kernels (r
 // lmat(p) = p*p rounded up to a multiple of 4 entries and every vector block to
 // lvec(p) = p rounded up to 4, so that each block starts 16-byte aligned (FP32
 // kernels read the blocks with 128-bit loads):
-//   [M][K][Mi][Kc] (lmat each) [dL][dR][dLh][dRh] (lvec each) [h][t][ts][dTL][dTR][0][0][0]
-//   [Qc] (lmat) [mL][mR][qL][qR] (lvec each)
+//   [M][K][Mi][Kc] (lmat each) [dL][dR][dLh][dRh] (lvec each) [h][t][ts][dTL][dTR][cs][0][0]
+//   [Qc] (lmat) [mL][mR][qL][qR] (lvec each) [EQc][EKc][EM] (lmat each)
+// cs = 1 marks a centrosymmetric layer (M, Kc and Qc unchanged by reversing
+// both indices: a uniform layer away from non-periodic boundaries); for p >= 5
+// the E* blocks then hold the even-odd form of Qc, Kc and M (eo_pack), with
+// which a contraction takes h (h + p mod 2) + h^2 + (p odd ? h + 1 : 0)
+// multiply-adds plus 2p additions instead of p^2 (h = p / 2).
 inline int lmat(int p) { return (p * p + 3) / 4 * 4; }
 inline int lvec(int p) { return (p + 3) / 4 * 4; }
-inline int lstride(int p) { return 5 * lmat(p) + 8 * lvec(p) + 8; }
+inline int lstride(int p) { return 8 * lmat(p) + 8 * lvec(p) + 8; }
 inline int lay_M(int) { return 0; }
 inline int lay_K(int p) { return lmat(p); }
 inline int lay_Mi(int p) { return 2 * lmat(p); }
@@ -65,6 +70,10 @@ inline int lay_mL(int p) { return 5 * lmat(p) + 4 * lvec(p) + 8; }
 inline int lay_mR(int p) { return 5 * lmat(p) + 5 * lvec(p) + 8; }
 inline int lay_qL(int p) { return 5 * lmat(p) + 6 * lvec(p) + 8; }
 inline int lay_qR(int p) { return 5 * lmat(p) + 7 * lvec(p) + 8; }
+inline int lay_cs(int p) { return 4 * lmat(p) + 4 * lvec(p) + 5; }
+inline int lay_EQc(int p) { return 5 * lmat(p) + 8 * lvec(p) + 8; }
+inline int lay_EKc(int p) { return 6 * lmat(p) + 8 * lvec(p) + 8; }
+inline int lay_EM(int p) { return 7 * lmat(p) + 8 * lvec(p) + 8; }
 
 // Geometry arguments shared by all cell kernels (passed by value).
 template <typename T>
@@ -117,6 +126,7 @@ struct Mesh {
   double* dgen_face = nullptr;
   double* dgen_tau = nullptr;
   bool general() const { return desc.map == SIPG_MAP_PERTURBED; }
+  bool eo_xz = false;  // every x- and z-layer centrosymmetric (even-odd contractions, p >= 5)
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
   int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)

@@ -192,6 +192,40 @@ bool invert(int p, const std::vector<long double>& A, std::vector<long double>& 
 
 }  // namespace
 
+// A[a][b] = A[p-1-a][p-1-b] up to rounding (1e-13 of the largest entry)
+static bool centrosymmetric(int p, const double* A) {
+  double mx = 0.0, d = 0.0;
+  for (int i = 0; i < p * p; ++i) mx = std::fmax(mx, std::fabs(A[i]));
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b) d = std::fmax(d, std::fabs(A[a * p + b] - A[(p - 1 - a) * p + (p - 1 - b)]));
+  return d <= 1e-13 * mx;
+}
+
+// Even-odd form of a centrosymmetric p x p matrix A (Solomonoff's splitting):
+// with h = p / 2, e_b = v_b + v_(p-1-b), o_b = v_b - v_(p-1-b) (b < h) and,
+// for odd p, the middle value v_h, the product y = A v is
+//   s_a = sum_b E[a][b] e_b (+ E[a][h] v_h),  d_a = sum_b O[a][b] o_b,
+//   y_a = s_a + d_a,  y_(p-1-a) = s_a - d_a  (a < h),
+//   y_h = sum_b Z[b] e_b + Z[h] v_h  (odd p),
+// E[a][b] = (A[a][b] + A[a][p-1-b]) / 2, E[a][h] = A[a][h], O[a][b] =
+// (A[a][b] - A[a][p-1-b]) / 2, Z = the middle row.  Packed as E (h x (h + odd)),
+// O (h x h), Z (h + 1 for odd p), from the symmetrised A.
+static void eo_pack(int p, const double* A, double* out) {
+  const int h = p / 2, odd = p & 1;
+  auto S = [&](int a, int b) { return 0.5L * ((long double)A[a * p + b] + A[(p - 1 - a) * p + (p - 1 - b)]); };
+  int k = 0;
+  for (int a = 0; a < h; ++a) {
+    for (int b = 0; b < h; ++b) out[k++] = (double)(0.5L * (S(a, b) + S(a, p - 1 - b)));
+    if (odd) out[k++] = (double)S(a, h);
+  }
+  for (int a = 0; a < h; ++a)
+    for (int b = 0; b < h; ++b) out[k++] = (double)(0.5L * (S(a, b) - S(a, p - 1 - b)));
+  if (odd) {
+    for (int b = 0; b < h; ++b) out[k++] = (double)S(h, b);
+    out[k++] = (double)S(h, h);
+  }
+}
+
 int build_tables(Mesh& m) {
   const int p = m.p;
   std::vector<double> zn, wn, zq, wq;
@@ -294,6 +328,15 @@ int build_tables(Mesh& m) {
         L[lay_qL(p) + a] = (double)ql;
         L[lay_qR(p) + a] = (double)qr;
       }
+      // centrosymmetric layers: the even-odd forms of Qc, Kc and M
+      const bool cs = p >= 5 && centrosymmetric(p, L + lay_M(p)) && centrosymmetric(p, L + lay_Kc(p)) &&
+                      centrosymmetric(p, L + lay_Qc(p));
+      L[lay_cs(p)] = cs ? 1.0 : 0.0;
+      if (cs) {
+        eo_pack(p, L + lay_Qc(p), L + lay_EQc(p));
+        eo_pack(p, L + lay_Kc(p), L + lay_EKc(p));
+        eo_pack(p, L + lay_M(p), L + lay_EM(p));
+      }
     }
     // penalty shares and face increments (Eq. (taue), Eq. (tau))
     const double s = m.penalty * (m.k + 1) * (m.k + 1);
@@ -309,6 +352,11 @@ int build_tables(Mesh& m) {
       tab[(size_t)i * st + lay_dTR(p)] = tr > ts ? tr - ts : 0.0;
     }
   }
+  // even-odd contractions along x and z when all their layers allow it
+  m.eo_xz = p >= 5;
+  for (int dir : {0, 2})
+    for (int i = 0; i < m.desc.n[dir]; ++i)
+      if (m.htab[dir][(size_t)i * st + lay_cs(p)] == 0.0) m.eo_xz = false;
   // over-integration tables of the convective term
   {
     const int Q = (3 * m.k) / 2 + 1;

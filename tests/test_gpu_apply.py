@@ -319,6 +319,38 @@ def test_inverse_mass_double_float(k):
     assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
 
 
+def test_autotune_json_cache(tmp_path):
+    """The autotuner's choice goes to a JSON cache keyed by degree, precision,
+    map, mesh size and arithmetic; a second mesh reads it back (same cells per
+    block and FP32 thread mapping) without re-timing; results stay at parity."""
+    import json
+    from paper_1607_01323_gb300 import apply_laplace_f32, apply_laplace_f64, autotune
+    c = channel((6, 4, 3))
+    k = 3
+    cache = str(tmp_path / "tune.json")
+    m = gpu_mesh(c, k)
+    c0 = autotune(m, 0, cache)
+    c1 = autotune(m, 1, cache)
+    m.set_f64_arithmetic("double_float")
+    c2 = autotune(m, 0, cache)
+    data = json.load(open(cache))
+    assert len(data) == 3 and all(set(v) == {"cpb", "mapping"} for v in data.values())
+    assert {v["cpb"] for v in data.values()} >= {c0}
+    m2 = gpu_mesh(c, k)
+    assert autotune(m2, 0, cache) == c0 and autotune(m2, 1, cache) == c1
+    assert m2.cells_per_block(1) == m.cells_per_block(1)
+    m2.set_f64_arithmetic("double_float")
+    assert autotune(m2, 0, cache) == c2
+    op = SIPG(oracle_spec(c), k)
+    A = op.assemble()
+    x = uniform(m2.n_dofs, "x")
+    norm_a = abs(A).sum(axis=1).max()
+    assert scaled_err(apply_laplace_f64(m2, _cuda(x)).cpu().numpy(), A @ x, norm_a, x) <= TOL64
+    x32 = x.astype(np.float32)
+    y32 = apply_laplace_f32(m2, _cuda(x32, torch.float32)).cpu().numpy()
+    assert scaled_err(y32, A @ x32.astype(np.float64), norm_a, x) <= TOL32
+
+
 def test_geometry_matches_oracle():
     for c, k in [(channel((3, 6, 2), gamma=2.25), 4), (case((2, 2, 3), lo=(-1, 0, 2), hi=(1, 3, 5)), 2)]:
         op = SIPG(oracle_spec(c), k)
