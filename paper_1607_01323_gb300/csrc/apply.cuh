@@ -711,7 +711,7 @@ __device__ __forceinline__ void line_op_q(T (&w)[P], const T (&u)[P], const T* _
 template <typename T, int P>
 struct UniformMinBlocks {
   static constexpr int value = std::is_same<T, dfl>::value ? (P <= 5 ? 3 : (P <= 7 ? 2 : 1))
-                               : (std::is_same<T, float>::value ? (P <= 6 ? 4 : (P == 7 ? 3 : 2)) : (P <= 6 ? 2 : 1));
+                               : (std::is_same<T, float>::value ? (P <= 6 ? 4 : (P == 7 ? 3 : 2)) : (P <= 5 ? 3 : (P <= 6 ? 2 : 1)));
 };
 
 // Shared memory of apply_uniform_kernel: own cells (kept to the end for the
