@@ -373,40 +373,42 @@ __device__ __forceinline__ void store_line(T* base, const T (&v)[P], int start, 
   for (int a = 0; a < P; ++a) base[start + a * step] = v[a];
 }
 
-// Block reduction of three doubles; thread 0 writes out[0..2].
-__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out) {
+// Block reduction of NV doubles (the others of the three written as 0);
+// thread 0 writes out[0..2].  Every add is an FP64 instruction, which costs
+// as much as a multiply-add of the operator on this GPU, so only the values
+// in use are reduced, and the second level covers only the block's warps.
+template <int NV>
+__device__ __forceinline__ void block_reduce_n(double a, double b, double c, double* out) {
   __shared__ double red[3][32];
+  double v[3] = {a, b, c};
   __syncthreads();  // a previous call may still read red
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
-  }
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][wid] = a;
-    red[1][wid] = b;
-    red[2][wid] = c;
-  }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[k][wid] = v[k];
   __syncthreads();
   if (wid == 0) {
     const int nw = (blockDim.x + 31) >> 5;
-    a = lane < nw ? red[0][lane] : 0.0;
-    b = lane < nw ? red[1][lane] : 0.0;
-    c = lane < nw ? red[2][lane] : 0.0;
 #pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = lane < nw ? red[k][lane] : 0.0;
     for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      c += __shfl_down_sync(0xffffffffu, c, o);
+      if (o < nw) {  // uniform across the warp
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+      }
     }
     if (lane == 0) {
-      out[0] = a;
-      out[1] = b;
-      out[2] = c;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) out[k] = k < NV ? v[k] : 0.0;
     }
   }
+}
+__device__ __forceinline__ void block_reduce3(double a, double b, double c, double* out) {
+  block_reduce_n<3>(a, b, c, out);
 }
 
 // Partial sums of one block to the sink; the last block of the grid adds all
@@ -415,7 +417,10 @@ __device__ __forceinline__ void block_reduce3(double a, double b, double c, doub
 __device__ __forceinline__ void sink_dots(const DotSink& s, double a, double b, double c) {
   const unsigned nb = gridDim.x * gridDim.y;
   const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
-  block_reduce3(a, b, c, s.partials + 3 * (long long)bid);
+  if (s.sums)
+    block_reduce_n<3>(a, b, c, s.partials + 3 * (long long)bid);
+  else
+    block_reduce_n<1>(a, b, c, s.partials + 3 * (long long)bid);
   if (!s.counter) return;
   __shared__ int last;
   if (threadIdx.x == 0) {
@@ -440,7 +445,10 @@ __device__ __forceinline__ void sink_dots(const DotSink& s, double a, double b, 
     for (unsigned i = threadIdx.x; i < nb; i += blockDim.x) x += __ldcg(s.partials + 3 * i);
   }
   double t[3];
-  block_reduce3(x, y, z, t);  // thread 0 holds the totals
+  if (s.sums)  // thread 0 holds the totals
+    block_reduce_n<3>(x, y, z, t);
+  else
+    block_reduce_n<1>(x, y, z, t);
   if (threadIdx.x == 0) {
     s.totals[0] = t[0];
     s.totals[1] = t[1];
@@ -845,11 +853,14 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   }
   __syncthreads();
   double d_xy = 0.0, d_y = 0.0, d_x = 0.0;
+  T out[P];
+  int out_start = 0;
   if (active) {
     // phase X2 on the x-lines: Mx -> global (or the Chebyshev step)
     int start, step;
     line_geom<P>(0, ti, tj, start, step);
-    T v[P], out[P];
+    out_start = start;
+    T v[P];
     load_line<T, P>(v, v1, start, step);
     const T* Lx = g.tab[0] + id[0] * O::stride;
     matvec_l<T, P>(out, Lx, O::M, O::EM, EOX, v);
@@ -870,12 +881,9 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
         epi.x[o + a] += di;
       }
     } else {
-      S* yo = y + cbase + (long long)e * P3 + start;
 #pragma unroll
-      for (int a = 0; a < P; ++a) {
+      for (int a = 0; a < P; ++a)
         if (do_scale) out[a] *= scale;
-        yo[a] = cvt_out<S, T>(out[a], sc);
-      }
     }
     if (!CHEB && dots) {
       // line sums in the compute type, one conversion per line; the x-line of
@@ -897,7 +905,17 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
       d_x = cvt_out<double, T>(sx, sc);
     }
   }
+  // the block's partial sums go out (and are fenced) before the block writes
+  // y, so that the fence waits for the partials only; y is read by later
+  // kernels, after this one has finished
   if (dots) sink_dots(sink, d_xy, d_y, d_x);
+  if constexpr (!CHEB) {
+    if (active) {
+      S* yo = y + cbase + (long long)e * P3 + out_start;
+#pragma unroll
+      for (int a = 0; a < P; ++a) yo[a] = cvt_out<S, T>(out[a], sc);
+    }
+  }
 }
 
 // Plane variant of the uniform-viscosity operator for FP32 (the line variant
