@@ -118,6 +118,40 @@ __device__ void block_partial3(double a, double b, double c, double* out) {
   }
 }
 
+// Partials of one CG update block: |r|^2 (accumulated in FP32 from the top
+// 24 bits of r; it only feeds the stopping test) reduced with FP32 shuffles,
+// r.z and, when ZQ, z.q with FP64 shuffles (every FP64 add costs as much as a
+// multiply-add of the update itself on this GPU).
+template <bool ZQ>
+__device__ void block_partial_update(float rr, double rz, double zq, double* out) {
+  __shared__ float shr[32];
+  __shared__ double shd[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+    rz += __shfl_down_sync(0xffffffffu, rz, o);
+    if (ZQ) zq += __shfl_down_sync(0xffffffffu, zq, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    shr[wid] = rr;
+    shd[0][wid] = rz;
+    shd[1][wid] = ZQ ? zq : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s0 = 0.f;
+    double s1 = 0.0, s2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      s0 += shr[w];
+      s1 += shd[0][w];
+      if (ZQ) s2 += shd[1][w];
+    }
+    out[3 * blockIdx.x] = (double)s0;
+    out[3 * blockIdx.x + 1] = s1;
+    out[3 * blockIdx.x + 2] = s2;
+  }
+}
+
 // FP32 value of the top 24 mantissa bits of a double (truncation, by bit
 // manipulation: no FP64 instruction); 0 below the normal FP32 range, +inf above
 // it and for inf / NaN (so a non-finite residual still stops the solver).
@@ -281,8 +315,7 @@ __global__ void k_update(Scalars* sc, long long n, double* __restrict__ x, doubl
   } else {
     for (long long i = t0; i < n; i += stride) one(i);
   }
-  const double rr = (double)rr32;
-  block_partial3(rr, rz, zq, part);
+  block_partial_update<ZQ>(rr32, rz, zq, part);
   if (!FORM_Z) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       sc->alpha = alpha;
