@@ -167,54 +167,83 @@ def bench_config(world=1):
     return dict(BENCH_CONFIG, parallelism="replicas" if world > 1 else "single")
 
 
+# The oracle timings of the five configurations: mesh, degree, components,
+# operator coefficients and the sampled fraction of the cells (about a second
+# of single-core oracle work per sampled apply).
+_CH = dict(lo=(0.0, -1.0, 0.0), hi=(2 * math.pi, 1.0, math.pi), mapping="channel", gamma=1.8)
+ORACLE_CONFIGS = {
+    "c1": dict(n=(4, 4, 4), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), bc=("periodic",) * 3, mapping="affine",
+               gamma=1.8, k=3, ncomp=1, frac=1.0, kw={}, label="4^3 periodic cube, k=3, Laplace"),
+    "c2": dict(WORKLOAD, bc=None, ncomp=1, frac=1.0 / 16, kw={}, label="32^3 k=4 channel Poisson operator"),
+    "c3": dict(_CH, n=(64, 64, 64), bc=("periodic", "dirichlet", "periodic"), k=3, ncomp=3, frac=1.0 / 256,
+               kw=dict(mass_coef=1500.0, nu=1 / 180), label="64^3 k=3 channel Helmholtz, 3 components"),
+    "c4": dict(_CH, n=(48, 48, 48), bc=("periodic", "neumann", "periodic"), k=5, ncomp=1, frac=1.0 / 128, kw={},
+               label="48^3 k=5 Neumann channel Laplacian"),
+    "c5": dict(_CH, n=(32, 32, 32), bc=("periodic", "dirichlet", "periodic"), k=3, ncomp=1, frac=1.0 / 32,
+               kw=dict(mass_coef=1500.0, nu_cell="lognormal"), label="32^3 k=3 channel Helmholtz, per-cell nu"),
+}
+
 _ORACLE = {}
 
 
-def _oracle_state(frac):
-    """The oracle operator of the bench problem, its seeded cell sample and its
+def _oracle_state(frac, cfg="c2"):
+    """The oracle operator of a configuration, its seeded cell sample and an
     input (cached per process)."""
-    if frac not in _ORACLE:
+    key = (cfg, frac)
+    if key not in _ORACLE:
         import numpy as np
         from oracle.mesh import MeshSpec
         from oracle.sipg import SIPG
         from paper_1607_01323_gb300 import inputs
-        w = WORKLOAD
-        spec = MeshSpec(*w["n"], lo=w["lo"], hi=w["hi"], bc_lo=w["bc_lo"], bc_hi=w["bc_hi"], mapping=w["mapping"],
-                        gamma=w["gamma"])
+        c = ORACLE_CONFIGS[cfg]
+        bc_lo = c["bc"] if c["bc"] else c["bc_lo"]
+        bc_hi = c["bc"] if c["bc"] else c["bc_hi"]
+        spec = MeshSpec(*c["n"], lo=c["lo"], hi=c["hi"], bc_lo=bc_lo, bc_hi=bc_hi, mapping=c["mapping"],
+                        gamma=c["gamma"])
         t0 = time.time()
-        op = SIPG(spec, w["k"])
+        op = SIPG(spec, c["k"])
         setup = time.time() - t0
         ncell = spec.ncell
-        pick = inputs.u64(0, "oracle_sample", 0, int(ncell * frac)) % np.uint64(ncell)
-        cells = np.unique(pick.astype(np.int64))
-        X = op.node_coordinates().reshape(-1, 3)
-        _ORACLE[frac] = dict(op=op, cells=cells, x=manufactured_f(X), setup=setup, ncell=ncell)
-    return _ORACLE[frac]
+        if frac >= 1.0:
+            cells = np.arange(ncell)
+        else:
+            pick = inputs.u64(0, "oracle_sample", 0, int(ncell * frac)) % np.uint64(ncell)
+            cells = np.unique(pick.astype(np.int64))
+        if cfg == "c2":
+            X = op.node_coordinates().reshape(-1, 3)
+            x = manufactured_f(X)
+        else:
+            x = inputs.uniform(0, "x", c["ncomp"] * ncell * op.P).reshape(c["ncomp"], -1)
+        kw = dict(c["kw"])
+        if kw.get("nu_cell") == "lognormal":
+            kw["nu_cell"] = np.exp(0.5 * inputs.normal(0, "xi", ncell)) / 180.0
+        _ORACLE[key] = dict(op=op, cells=cells, x=x, kw=kw, setup=setup, ncell=ncell)
+    return _ORACLE[key]
 
 
-def _oracle_apply_part(frac, part, nparts):
+def _oracle_apply_part(frac, part, nparts, cfg="c2"):
     """One oracle apply restricted to the part-th of nparts slices of the sampled
     cells (a process-pool task); returns the process CPU seconds it used."""
     import numpy as np
-    st = _oracle_state(frac)
+    st = _oracle_state(frac, cfg)
     mask = np.zeros(st["ncell"], dtype=bool)
     mask[st["cells"][part::nparts]] = True
     c0 = time.process_time()
-    st["op"].apply(st["x"], targets=mask)
+    st["op"].apply(st["x"], targets=mask, **st["kw"])
     return time.process_time() - c0
 
 
 class OracleSample:
     """The oracle as it stands (dense-quadrature element-by-element FP64 apply)
-    on the same 32^3 k=4 channel problem, bounded: each timed unit is one
-    operator apply restricted to a fixed seeded sample of ``frac`` of the cells,
-    counted as (sampled DoFs) per second, i.e. the same DoF/s of operator apply.
-    With workers > 1 the sample is split over that many spawned processes (one
-    per host core); the oracle's CG adds only vector operations around its
-    applies."""
+    on one of the configurations (default: the bench's 32^3 k=4 channel
+    problem), bounded: each timed unit is one operator apply restricted to a
+    fixed seeded sample of ``frac`` of the cells, counted as (sampled DoFs) per
+    second, i.e. the same DoF/s of operator apply.  With workers > 1 the
+    sample is split over that many spawned processes (one per host core); the
+    oracle's CG adds only vector operations around its applies."""
 
-    def __init__(self, frac=1.0 / 16, workers=1):
-        self.frac, self.workers = frac, workers
+    def __init__(self, frac=1.0 / 16, workers=1, cfg="c2"):
+        self.frac, self.workers, self.cfg = frac, workers, cfg
         self.pool = None
         if workers > 1:
             import multiprocessing as mp
@@ -226,7 +255,7 @@ class OracleSample:
             try:
                 self.pool = ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
                 t0 = time.time()
-                list(self.pool.map(_oracle_state, [frac] * workers))
+                list(self.pool.map(_oracle_state, [frac] * workers, [cfg] * workers))
                 self.setup = time.time() - t0
             finally:
                 for k, v in saved.items():
@@ -234,21 +263,22 @@ class OracleSample:
                         os.environ.pop(k, None)
                     else:
                         os.environ[k] = v
-            st = _oracle_state_meta(frac)
+            st = _oracle_state_meta(frac, cfg)
         else:
-            st = _oracle_state(frac)
+            st = _oracle_state(frac, cfg)
             self.setup = st["setup"]
-        self.ncells = len(st["cells"])
-        self.sample_dofs = self.ncells * (WORKLOAD["k"] + 1) ** 3
+        c = ORACLE_CONFIGS[cfg]
+        self.ncells, self.ncell = len(st["cells"]), st["ncell"]
+        self.sample_dofs = self.ncells * (c["k"] + 1) ** 3 * c["ncomp"]
 
     def step(self):
         """(wall seconds, CPU seconds) of one sampled apply."""
         t0 = time.time()
         if self.pool is None:
-            cpu = _oracle_apply_part(self.frac, 0, 1)
+            cpu = _oracle_apply_part(self.frac, 0, 1, self.cfg)
         else:
-            cpu = sum(self.pool.map(_oracle_apply_part, [self.frac] * self.workers, range(self.workers),
-                                    [self.workers] * self.workers))
+            n = self.workers
+            cpu = sum(self.pool.map(_oracle_apply_part, [self.frac] * n, range(n), [n] * n, [self.cfg] * n))
         return time.time() - t0, cpu
 
     def close(self):
@@ -257,23 +287,27 @@ class OracleSample:
             self.pool = None
 
     def describe(self, n, wall):
-        return ("%d oracle FP64 applies restricted to a seeded sample of %d of 32768 cells (%d DoF each) of the "
-                "32^3 k=4 channel Poisson operator on %d process(es), %.1f s wall after %.1f s oracle setup; "
-                "sampled DoF per second" % (n, self.ncells, self.sample_dofs, self.workers, wall, self.setup))
+        return ("%d oracle FP64 applies restricted to a seeded sample of %d of %d cells (%d DoF each) of the "
+                "%s on %d process(es), %.1f s wall after %.1f s oracle setup; sampled DoF per second"
+                % (n, self.ncells, self.ncell, self.sample_dofs, ORACLE_CONFIGS[self.cfg]["label"], self.workers,
+                   wall, self.setup))
 
 
-def _oracle_state_meta(frac):
-    """The sampled cells of the bench problem without building the operator."""
+def _oracle_state_meta(frac, cfg="c2"):
+    """The sampled cells of a configuration without building the operator."""
     import numpy as np
     from paper_1607_01323_gb300 import inputs
-    ncell = WORKLOAD["n"][0] * WORKLOAD["n"][1] * WORKLOAD["n"][2]
+    n = ORACLE_CONFIGS[cfg]["n"]
+    ncell = n[0] * n[1] * n[2]
+    if frac >= 1.0:
+        return dict(cells=np.arange(ncell), ncell=ncell)
     pick = inputs.u64(0, "oracle_sample", 0, int(ncell * frac)) % np.uint64(ncell)
     return dict(cells=np.unique(pick.astype(np.int64)), ncell=ncell)
 
 
-def time_oracle(workers, max_seconds, frac=1.0 / 16, warmup=1, steps=None):
+def time_oracle(workers, max_seconds, frac=None, warmup=1, steps=None, cfg="c2"):
     """Sampled oracle applies on `workers` processes: the DoF/s and its record."""
-    s = OracleSample(frac, workers)
+    s = OracleSample(ORACLE_CONFIGS[cfg]["frac"] if frac is None else frac, workers, cfg)
     try:
         for _ in range(warmup):
             s.step()
@@ -670,6 +704,40 @@ def _timed(fn, reps=3):
     return statistics.median(ts), out
 
 
+def run_oracle_timings(args):
+    """The oracle (as it stands) on the GPU host's cores, every configuration:
+    the sampled FP64 apply on all cores (one spawned process per core) and on
+    one core; the oracle's Jacobi-PCG solve to 1e-10 for the 4^3 cube
+    (assembled CSR, one core) and, for the bench's 32^3 k=4 problem, the time
+    of one full all-core apply times the GPU solve's 342 iterations (the
+    oracle's CG adds only vector operations around its applies)."""
+    import numpy as np
+    ncpu = os.cpu_count() or 1
+    out = {"workload": "oracle", "host_cpus": ncpu, "applies": {}}
+    for cfg in ("c1", "c2", "c3", "c4", "c5"):
+        va, ra, _ = time_oracle(ncpu, args.oracle_seconds, cfg=cfg)
+        v1, r1, _ = time_oracle(1, args.oracle_seconds, cfg=cfg)
+        out["applies"][cfg] = {"all_cores_dofs_per_s": va, "one_core_dofs_per_s": v1, "cores_used": ra["cores"],
+                               "sample_all_cores": ra["sample"], "sample_one_core": r1["sample"]}
+    # oracle Jacobi-PCG on the 4^3 periodic cube, k = 3 (zero-mean rhs)
+    from oracle import solvers
+    st = _oracle_state(1.0, "c1")
+    A = st["op"].assemble()
+    b = st["x"][0] - st["x"][0].mean()
+    t0 = time.time()
+    xs, it, rel = solvers.cg(lambda v: A @ v, b, rtol=1e-10, zero_mean=True, precond=lambda r: r / A.diagonal())
+    out["cg_c1"] = {"seconds": time.time() - t0, "iters": it, "relres": rel, "cores": 1,
+                    "note": "assembled CSR (4096 unknowns), Jacobi-PCG to 1e-10, zero-mean rhs"}
+    # the bench problem: one full apply on all cores, times the GPU solve's iterations
+    va, ra, wall = time_oracle(ncpu, None, frac=1.0, warmup=0, steps=1, cfg="c2")
+    t_apply = 4096000 / va
+    out["cg_c2_estimate"] = {"seconds_per_apply_all_cores": t_apply, "iters": 342,
+                             "estimated_solve_s": 343 * t_apply, "sample": ra["sample"],
+                             "note": "one full oracle apply of the 32^3 k=4 Poisson operator on all cores times "
+                                     "the 343 applies of the 1e-10 Jacobi-PCG solve (the GPU's iteration count)"}
+    print(json.dumps(out))
+
+
 def run_config(args):
     """Timings of the other workload configurations (one JSON line each):
     c1: the 4^3 periodic unit cube at k=3 (operator apply only);
@@ -906,6 +974,8 @@ def main():
     ap.add_argument("--mode", default="solve", choices=["solve", "apply", "vcycle", "convective", "solve_only"],
                     help="apply: only operator applies; vcycle: only multigrid V-cycles; convective: only "
                          "convective-term applies; solve_only: only CG solves of the bench problem")
+    ap.add_argument("--oracle-seconds", type=float, default=6.0,
+                    help="seconds of sampled oracle applies per measurement of --workload oracle")
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "gmg_f32", "none", "invmass"],
                     help="preconditioner of --mode solve_only")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
@@ -916,7 +986,7 @@ def main():
                     help="arithmetic of the FP64 operator of the timed solves (native FP64, the default, or "
                          "double_float: FP32 pairs on the FP32 pipes)")
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c4", "c5", "v3c", "ns", "perturbed", "mg_scaling"],
+                    choices=["c1", "c2", "c3", "c4", "c5", "v3c", "ns", "perturbed", "mg_scaling", "oracle"],
                     help="c2 (default) is the bench step; c1, c3-c5, v3c, ns print timings of other workloads")
     args = ap.parse_args()
     if args.mode == "apply":
@@ -927,6 +997,8 @@ def main():
         run_convective_only(args)
     elif args.mode == "solve_only":
         run_solve_only(args)
+    elif args.workload == "oracle":
+        run_oracle_timings(args)
     elif args.workload != "c2":
         run_config(args)
     elif args.impl == "reference":
