@@ -192,11 +192,10 @@ bool invert(int p, const std::vector<long double>& A, std::vector<long double>& 
 
 }  // namespace
 
-// A[a][b] = A[p-1-a][p-1-b] up to the rounding of the table computation.
-// The layer's nodes are global coordinates, so a uniform layer far from the
-// origin carries asymmetric rounding of order (layer index) x 1e-16 relative,
-// amplified by the inverse mass in Qc (3e-14 at layer 30 of 32): the test
-// allows 1e-12 of the largest entry, and eo_pack symmetrises.
+// A[a][b] = A[p-1-a][p-1-b] up to the rounding of the table computation
+// (about 1e-15 of the largest entry for a uniform layer, whose nodes are
+// taken relative to its start; graded layers are far from symmetric): the
+// test allows 1e-12, and eo_pack symmetrises.
 static bool centrosymmetric(int p, const double* A) {
   double mx = 0.0, d = 0.0;
   for (int i = 0; i < p * p; ++i) mx = std::fmax(mx, std::fabs(A[i]));
@@ -263,7 +262,14 @@ int build_tables(Mesh& m) {
     for (int i = 0; i < n; ++i) {
       double* L = &tab[(size_t)i * st];
       std::vector<long double> X(p);
-      for (int a = 0; a < p; ++a) X[a] = map_coord(m.desc, dir, (i + zn[a]) / n);
+      // every entry depends on the layer's own geometry only: affine directions
+      // take the nodes relative to the layer's start (exact, the same for every
+      // uniform layer), the graded direction the map's global values
+      const bool affine_dir =
+          !(dir == 1 && (m.desc.map == SIPG_MAP_CHANNEL_TANH || m.desc.map == SIPG_MAP_CHANNEL_LINEAR));
+      for (int a = 0; a < p; ++a)
+        X[a] = affine_dir ? (long double)(m.desc.hi[dir] - m.desc.lo[dir]) * zn[a] / n
+                          : (long double)map_coord(m.desc, dir, (i + zn[a]) / n);
       // derivative of the degree-k interpolant of the map at the Gauss points and ends
       std::vector<long double> J(p, 0.0L);
       long double J0 = 0.0L, J1 = 0.0L;
