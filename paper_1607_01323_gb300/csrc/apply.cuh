@@ -853,38 +853,19 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   }
   __syncthreads();
   double d_xy = 0.0, d_y = 0.0, d_x = 0.0;
-  T out[P];
-  int out_start = 0;
   if (active) {
-    // phase X2 on the x-lines: Mx -> global (or the Chebyshev step)
+    // phase X2 on the x-lines: Mx -> V2 (the block's result, written to
+    // global memory below in one coalesced sweep)
     int start, step;
     line_geom<P>(0, ti, tj, start, step);
-    out_start = start;
-    T v[P];
+    T v[P], out[P];
     load_line<T, P>(v, v1, start, step);
     const T* Lx = g.tab[0] + id[0] * O::stride;
     matvec_l<T, P>(out, Lx, O::M, O::EM, EOX, v);
-    if constexpr (CHEB) {
-      static_assert(std::is_same<T, float>::value && std::is_same<S, float>::value, "FP32 only");
-      // t = A d for this x-line; d (the input) from the staged cell
-      T dold[P];
-      load_line<T, P>(dold, us, start, step);
-      const long long o = cbase + (long long)e * P3 + start;
 #pragma unroll
-      for (int a = 0; a < P; ++a) {
-        T tt = out[a];
-        if (do_scale) tt *= scale;
-        const float ri = epi.r[o + a] - tt;
-        const float di = epi.c1 * dold[a] + epi.c2 * ri * epi.dinv[o + a];
-        epi.r[o + a] = ri;
-        epi.dnew[o + a] = di;
-        epi.x[o + a] += di;
-      }
-    } else {
-#pragma unroll
-      for (int a = 0; a < P; ++a)
-        if (do_scale) out[a] *= scale;
-    }
+    for (int a = 0; a < P; ++a)
+      if (do_scale) out[a] *= scale;
+    store_line<T, P>(v2, out, start, step);  // V2 is free since phase Z
     if (!CHEB && dots) {
       // line sums in the compute type, one conversion per line; the x-line of
       // the input from the staged cell
@@ -909,11 +890,23 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   // y, so that the fence waits for the partials only; y is read by later
   // kernels, after this one has finished
   if (dots) sink_dots(sink, d_xy, d_y, d_x);
-  if constexpr (!CHEB) {
-    if (active) {
-      S* yo = y + cbase + (long long)e * P3 + out_start;
-#pragma unroll
-      for (int a = 0; a < P; ++a) yo[a] = cvt_out<S, T>(out[a], sc);
+  __syncthreads();
+  // the block's cells are contiguous in memory: consecutive threads write
+  // (or, for the Chebyshev step, update) consecutive entries
+  const long long o0 = cbase + cell0 * P3;
+  for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) {
+    const T tv = s2[idx];
+    if constexpr (CHEB) {
+      static_assert(std::is_same<T, float>::value && std::is_same<S, float>::value, "FP32 only");
+      // r -= A d, dnew = c1 d + c2 D^-1 r, x += dnew with d the staged input
+      const long long o = o0 + idx;
+      const float ri = epi.r[o] - tv;
+      const float di = epi.c1 * su[idx] + epi.c2 * ri * epi.dinv[o];
+      epi.r[o] = ri;
+      epi.dnew[o] = di;
+      epi.x[o] += di;
+    } else {
+      y[o0 + idx] = cvt_out<S, T>(tv, sc);
     }
   }
 }
