@@ -72,6 +72,7 @@ Geo<T> make_geo(const Mesh& m) {
   }
   g.tau_scale = T(m.penalty * (m.k + 1) * (m.k + 1));
   g.dsc = m.dscale ? m.dscale + 2 : nullptr;
+  for (int d = 0; d < 3; ++d) g.lm[d] = m.lay_same[d] ? 0 : -1;
   return g;
 }
 template Geo<double> make_geo<double>(const Mesh&);

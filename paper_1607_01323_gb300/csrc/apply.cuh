@@ -363,8 +363,27 @@ __device__ __forceinline__ void load_line_global(T (&v)[P], const T* __restrict_
 template <typename T, typename S, int P>
 __device__ __forceinline__ void load_line_global_cvt(T (&v)[P], const S* __restrict__ base, int start, int step,
                                                      int sc) {
+  S r[P];  // all loads issued before the conversions
 #pragma unroll
-  for (int a = 0; a < P; ++a) v[a] = cvt_in<T, S>(__ldg(base + start + a * step), sc);
+  for (int a = 0; a < P; ++a) r[a] = __ldg(base + start + a * step);
+#pragma unroll
+  for (int a = 0; a < P; ++a) v[a] = cvt_in<T, S>(r[a], sc);
+}
+
+// dst[0..n) = src[0..n) converted to T, the whole block cooperating
+// (consecutive threads take consecutive entries), each thread issuing four
+// loads before it converts them
+template <typename T, typename S>
+__device__ __forceinline__ void stage_cvt(T* __restrict__ dst, const S* __restrict__ src, int n, int sc) {
+  const int bd = blockDim.x;
+  for (int i = threadIdx.x; i < n; i += 4 * bd) {
+    S r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r[j] = i + j * bd < n ? __ldg(src + i + j * bd) : S(0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (i + j * bd < n) dst[i + j * bd] = cvt_in<T, S>(r[j], sc);
+  }
 }
 
 template <typename T, int P>
@@ -523,7 +542,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) apply_kernel(Geo<T> g, const 
   {
     const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
     const S* xb = xc + cell0 * P3;
-    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx], sc);
+    stage_cvt<T, S>(su, xb, nc * P3, sc);
   }
   __syncthreads();
   T* us = su + cs * P3;
@@ -758,7 +777,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   const int sc = call_scale(g);
   {
     const S* xb = xc + cell0 * P3;
-    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx], sc);
+    stage_cvt<T, S>(su, xb, nc * P3, sc);
   }
   __syncthreads();
   T* us = su + cs * P3;
@@ -770,8 +789,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     id[0] = e % g.n[0];
     id[1] = (e / g.n[0]) % g.n[1];
     id[2] = e / (g.n[0] * g.n[1]);
-    tau_e = g.tab[0][id[0] * O::stride + O::ts] + g.tab[1][id[1] * O::stride + O::ts] +
-            g.tab[2][id[2] * O::stride + O::ts];
+    tau_e = g.tab[0][(id[0] & g.lm[0]) * O::stride + O::ts] + g.tab[1][(id[1] & g.lm[1]) * O::stride + O::ts] +
+            g.tab[2][(id[2] & g.lm[2]) * O::stride + O::ts];
   }
   const T tau2e = tau_e + tau_e;
   if (active) {
@@ -780,7 +799,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     for (int dir = 0; dir < 2; ++dir) {
       int start, step;
       line_geom<P>(dir, ti, tj, start, step);
-      const T* L = g.tab[dir] + id[dir] * O::stride;
+      const T* L = g.tab[dir] + (id[dir] & g.lm[dir]) * O::stride;
       int nbL, nbR, kL, kR, jl, jr;
       face_neighbor(g, dir, 0, id[dir], e, nbL, kL, jl);
       face_neighbor(g, dir, 1, id[dir], e, nbR, kR, jr);
@@ -802,8 +821,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
         else
           load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
       }
-      line_op_q<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
-                      kR == 0 ? g.tab[dir] + jr * O::stride : L, tau_e + L[O::dTR], tau2e, dir == 0 && EOX);
+      line_op_q<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + (jl & g.lm[dir]) * O::stride : L, tau_e + L[O::dTL], kR, uR,
+                      kR == 0 ? g.tab[dir] + (jr & g.lm[dir]) * O::stride : L, tau_e + L[O::dTR], tau2e, dir == 0 && EOX);
       store_line<T, P>(dir == 0 ? v1 : v2, w, start, step);
     }
   }
@@ -812,7 +831,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     // phase Z on the z-lines: Mz (V1 + V2 + mass_rel u) + w_z -> V1
     int start, step;
     line_geom<P>(2, ti, tj, start, step);
-    const T* L = g.tab[2] + id[2] * O::stride;
+    const T* L = g.tab[2] + (id[2] & g.lm[2]) * O::stride;
     constexpr bool eoz = EOX;
     int nbL, nbR, kL, kR, jl, jr;
     face_neighbor(g, 2, 0, id[2], e, nbL, kL, jl);
@@ -821,8 +840,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     load_line<T, P>(u, us, start, step);
     if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step, sc);
     if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
-    line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + jl * O::stride : L, tau_e + L[O::dTL], kR, uR,
-                    kR == 0 ? g.tab[2] + jr * O::stride : L, tau_e + L[O::dTR], tau2e, eoz);
+    line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + (jl & g.lm[2]) * O::stride : L, tau_e + L[O::dTL], kR, uR,
+                    kR == 0 ? g.tab[2] + (jr & g.lm[2]) * O::stride : L, tau_e + L[O::dTR], tau2e, eoz);
     T v[P], r[P];
     load_line<T, P>(v, v1, start, step);
     {
@@ -847,7 +866,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     line_geom<P>(1, ti, tj, start, step);
     T v[P], r[P];
     load_line<T, P>(v, v1, start, step);
-    const T* Ly = g.tab[1] + id[1] * O::stride;
+    const T* Ly = g.tab[1] + (id[1] & g.lm[1]) * O::stride;
     matvec_l<T, P>(r, Ly, O::M, O::EM, false, v);
     store_line<T, P>(v1, r, start, step);
   }
@@ -860,7 +879,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     line_geom<P>(0, ti, tj, start, step);
     T v[P], out[P];
     load_line<T, P>(v, v1, start, step);
-    const T* Lx = g.tab[0] + id[0] * O::stride;
+    const T* Lx = g.tab[0] + (id[0] & g.lm[0]) * O::stride;
     matvec_l<T, P>(out, Lx, O::M, O::EM, EOX, v);
 #pragma unroll
     for (int a = 0; a < P; ++a)
@@ -1134,7 +1153,7 @@ __global__ void __launch_bounds__(kMaxCellThreads) inverse_mass_kernel(Geo<T> g,
   {
     const int nc = (int)min((long long)cpb, (long long)g.ncell - cell0);
     const S* xb = x + cbase + cell0 * P3;
-    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) su[idx] = cvt_in<T, S>(xb[idx], sc);
+    stage_cvt<T, S>(su, xb, nc * P3, sc);
   }
   __syncthreads();
   T* us = su + cs * P3;

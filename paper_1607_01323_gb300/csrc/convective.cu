@@ -97,9 +97,18 @@ __global__ void __launch_bounds__(kConvThreads) convective_kernel(Geo<T> g, cons
     const int off = d == 0 ? off_W0 : (d == 1 ? off_W1 : off_W2);
     WJ(lc)[r] = tabs[off + id * Q + q];
   }
-  for (int i = threadIdx.x; i < cpb * 3 * P3; i += NT) {
-    const int lc = i / (3 * P3), r = i % (3 * P3), e = e0 + lc;
-    SU(lc)[r] = e < g.ncell ? cvt_in<T, double>(u[(r / P3) * N + (long long)e * P3 + r % P3], sc) : T(0);
+  for (int i0 = threadIdx.x; i0 < cpb * 3 * P3; i0 += 4 * NT) {
+    double v[4];  // all loads issued before the conversions
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = i0 + j * NT, lc = i / (3 * P3), r = i % (3 * P3), e = e0 + lc;
+      v[j] = i < cpb * 3 * P3 && e < g.ncell ? __ldg(u + (r / P3) * N + (long long)e * P3 + r % P3) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = i0 + j * NT, lc = i / (3 * P3), r = i % (3 * P3);
+      if (i < cpb * 3 * P3) SU(lc)[r] = cvt_in<T, double>(v[j], sc);
+    }
   }
   __syncthreads();
 

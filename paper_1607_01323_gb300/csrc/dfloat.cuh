@@ -7,8 +7,11 @@
 // operator evaluated in double-float on the FP32 pipes keeps the FP64 result
 // to the parity tolerance (1e-12 of ||A|| ||x||) at a fraction of the cost.
 //
-// Conversions to and from double use only integer and FP32 instructions (no
-// FP64 pipe) and carry a per-call power-of-two scale (below).
+// Conversions to and from double use integer and FP32 instructions (the FP64
+// pipe only on the rare out-of-range path of the unscaled conversion) and
+// carry a per-call power-of-two scale (below).  Kernels issue the loads of a
+// group of values before converting them: the out-of-line call of a rare
+// path would otherwise keep each load waiting for the previous conversion.
 #pragma once
 
 #include <cstdint>
@@ -187,8 +190,20 @@ __device__ __forceinline__ dfl df_from_double(double d, int s) {
   return dfl(hi, __int_as_float(__float_as_int(rf * __int_as_float((fe - 46) << 23)) | (int)sign));
 }
 
-// unscaled conversion: coefficients and geometry (their range is the mesh's)
-__device__ __forceinline__ dfl df_from_double(double d) { return df_from_double(d, 0); }
+// unscaled conversion of coefficients and geometry (their range is the
+// mesh's), all inline: the fast path of df_from_double(d, 0); a value whose
+// FP32 exponent leaves no room for a normal lo (|d| < 2^-80 or >= 2^128),
+// zero, inf or NaN becomes its FP32 rounding with lo = 0
+__device__ __forceinline__ dfl df_from_double(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int fe = (int)((u >> 52) & 0x7ff) - 1023 + 127;
+  if (__builtin_expect((unsigned)(fe - 47) > 207u, 0)) return dfl(__double2float_rn(d), 0.f);
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const float hi = __int_as_float((int)(sign | ((unsigned)fe << 23) | ((unsigned)(u >> 29) & 0x7fffffu)));
+  const unsigned r = (unsigned)(u >> 6) & 0x7fffffu;
+  const float rf = __int_as_float(0x4B000000 | (int)r) - 8388608.0f;
+  return dfl(hi, __int_as_float(__float_as_int(rf * __int_as_float((fe - 46) << 23)) | (int)sign));
+}
 
 // f 2^s as a double, the cases outside the common range: FP32 zeros and
 // subnormals (below the scaled range's resolution) give 0, inf / NaN stay

@@ -243,6 +243,16 @@ struct GenArgs {
   const int* skip;
 };
 
+// unscaled conversion of geometry and coefficients (their range is the mesh's;
+// inline, no out-of-line rare path: about 2,000 of them per cell)
+template <typename T>
+__device__ __forceinline__ T geo_in(double v) {
+  if constexpr (std::is_same<T, dfl>::value)
+    return df_from_double(v);
+  else
+    return (T)v;
+}
+
 template <int P>
 __host__ __device__ constexpr int gstride(int dir) {
   return dir == 0 ? 1 : (dir == 1 ? P : P * P);
@@ -262,18 +272,18 @@ __global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a
   const double* x = a.x + comp * N;
   int sc = 0;  // the call's scale exponent (double-float)
   if constexpr (std::is_same<T, dfl>::value) sc = a.g.dsc ? *a.g.dsc : 0;
-  for (int i = tid; i < P3; i += nt) su[i] = cvt_in<T, double>(x[(long long)e * P3 + i], sc);
+  stage_cvt<T, double>(su, x + (long long)e * P3, P3, sc);
   for (int i = tid; i < P2; i += nt) {
-    sS[i] = cvt_in<T, double>(a.head[i]);
-    sD[i] = cvt_in<T, double>(a.head[P2 + i]);
+    sS[i] = geo_in<T>(a.head[i]);
+    sD[i] = geo_in<T>(a.head[P2 + i]);
   }
   for (int i = tid; i < P; i += nt) {
-    sd0[i] = cvt_in<T, double>(a.head[2 * P2 + i]);
-    sd1[i] = cvt_in<T, double>(a.head[2 * P2 + P + i]);
+    sd0[i] = geo_in<T>(a.head[2 * P2 + i]);
+    sd1[i] = geo_in<T>(a.head[2 * P2 + P + i]);
   }
   __syncthreads();
-  const T cnu = cvt_in<T, double>(a.stiffness ? a.nu : 0.0), ccm = cvt_in<T, double>(a.cm);
-  const T fnu = cvt_in<T, double>(a.nu);
+  const T cnu = geo_in<T>(a.stiffness ? a.nu : 0.0), ccm = geo_in<T>(a.cm);
+  const T fnu = geo_in<T>(a.nu);
   const double* G = a.geo + (long long)e * 7 * P3;
   // x: A1 = S u, B1 = D u
   for (int l = tid; l < P2; l += nt) {
@@ -329,13 +339,13 @@ __global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a
         uq = fma(sS[q * P + i], vaa[i], uq);
       }
       const int pt = q * P2 + l;
-      const T g0 = cvt_in<T, double>(G[0 * P3 + pt]), g1 = cvt_in<T, double>(G[1 * P3 + pt]);
-      const T g2 = cvt_in<T, double>(G[2 * P3 + pt]), g3 = cvt_in<T, double>(G[3 * P3 + pt]);
-      const T g4 = cvt_in<T, double>(G[4 * P3 + pt]), g5 = cvt_in<T, double>(G[5 * P3 + pt]);
+      const T g0 = geo_in<T>(G[0 * P3 + pt]), g1 = geo_in<T>(G[1 * P3 + pt]);
+      const T g2 = geo_in<T>(G[2 * P3 + pt]), g3 = geo_in<T>(G[3 * P3 + pt]);
+      const T g4 = geo_in<T>(G[4 * P3 + pt]), g5 = geo_in<T>(G[5 * P3 + pt]);
       fx[q] = cnu * fma(g0, gx, fma(g1, gy, g2 * gz));
       fy[q] = cnu * fma(g1, gx, fma(g3, gy, g4 * gz));
       fz[q] = cnu * fma(g2, gx, fma(g4, gy, g5 * gz));
-      fm[q] = ccm * cvt_in<T, double>(G[6 * P3 + pt]) * uq;
+      fm[q] = ccm * geo_in<T>(G[6 * P3 + pt]) * uq;
     }
     for (int i = 0; i < P; ++i) {
       T s1 = T(0), s2 = T(0), s3 = T(0);
@@ -408,9 +418,13 @@ __global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a
         fv[1][j] = nd;
         if (kind == 0) {
           const double* xn = x + (long long)nb * P3;
-          fv[2][j] = cvt_in<T, double>(xn[nend * sd + tr], sc);
+          double xv[P];  // all loads issued before the conversions
+#pragma unroll
+          for (int i = 0; i < P; ++i) xv[i] = __ldg(xn + i * sd + tr);
+          fv[2][j] = cvt_in<T, double>(nend ? xv[P - 1] : xv[0], sc);
           T nn = T(0);
-          for (int i = 0; i < P; ++i) nn = fma(dnb[i], cvt_in<T, double>(xn[i * sd + tr], sc), nn);
+#pragma unroll
+          for (int i = 0; i < P; ++i) nn = fma(dnb[i], cvt_in<T, double>(xv[i], sc), nn);
           fv[3][j] = nn;
         }
       }
@@ -433,7 +447,7 @@ __global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a
       // flux at the face points
       const double* Fo = a.face + ((long long)e * 6 + f) * 4 * P2;
       const double* Fn = kind == 0 ? a.face + ((long long)nb * 6 + (2 * d + 1 - side)) * 4 * P2 : nullptr;
-      const T tau_f = cvt_in<T, double>(kind == 0 ? fmax(tau_e, a.tau[nb]) : tau_e), tau_o = cvt_in<T, double>(tau_e);
+      const T tau_f = geo_in<T>(kind == 0 ? fmax(tau_e, a.tau[nb]) : tau_e), tau_o = geo_in<T>(tau_e);
       for (int q = tid; q < P2; q += nt) {
         const int q1 = q % P, q2 = q / P;
         // val: u, d_d u of both sides; d1: t1-derivative; d2: t2-derivative
@@ -455,18 +469,18 @@ __global__ void __launch_bounds__(kGenThreads, 6) apply_general_kernel(GenArgs a
         go[d] = val[1];
         go[t1] = d1v[0];
         go[t2] = d2v[0];
-        const T fo0 = cvt_in<T, double>(Fo[0 * P2 + q]), fo1 = cvt_in<T, double>(Fo[1 * P2 + q]);
-        const T fo2 = cvt_in<T, double>(Fo[2 * P2 + q]);
+        const T fo0 = geo_in<T>(Fo[0 * P2 + q]), fo1 = geo_in<T>(Fo[1 * P2 + q]);
+        const T fo2 = geo_in<T>(Fo[2 * P2 + q]);
         const T dn_own = fma(go[0], fo0, fma(go[1], fo1, go[2] * fo2));
-        const T wda = cvt_in<T, double>(Fo[3 * P2 + q]);
+        const T wda = geo_in<T>(Fo[3 * P2 + q]);
         T rv, rg;
         if (kind == 0) {
           gn[d] = val[3];
           gn[t1] = d1v[1];
           gn[t2] = d2v[1];
           // the neighbour's g carries its own outward normal, -n
-          const T dn_nb = fma(gn[0], cvt_in<T, double>(Fn[0 * P2 + q]),
-                              fma(gn[1], cvt_in<T, double>(Fn[1 * P2 + q]), gn[2] * cvt_in<T, double>(Fn[2 * P2 + q])));
+          const T dn_nb = fma(gn[0], geo_in<T>(Fn[0 * P2 + q]),
+                              fma(gn[1], geo_in<T>(Fn[1 * P2 + q]), gn[2] * geo_in<T>(Fn[2 * P2 + q])));
           const T jump = val[0] - val[2];
           rv = tau_f * wda * jump - T(0.5) * (dn_own - dn_nb);
           rg = -(T(0.5) * jump);

@@ -493,8 +493,7 @@ __global__ void viscous_t_kernel(Geo<T> g, const T* __restrict__ Cg, const doubl
   const int e = blockIdx.x;
   const long long N = (long long)g.ncell * P3;
   const int xsc = call_scale(g);  // the call's scale exponent (double-float)
-  for (int i = threadIdx.x; i < 3 * P3; i += blockDim.x)
-    su[i] = cvt_in<T, double>(u[(i / P3) * N + (long long)e * P3 + i % P3], xsc);
+  for (int c = 0; c < 3; ++c) stage_cvt<T, double>(su + c * P3, u + c * N + (long long)e * P3, P3, xsc);
   stage_c<P>(Cg, C, Ct);
   __syncthreads();
   const CellCtxT<T> cc = cell_ctx<P>(g, e, (const T*)C, (const T*)Ct);
@@ -544,12 +543,17 @@ __global__ void viscous_t_kernel(Geo<T> g, const T* __restrict__ Cg, const doubl
           const int nend = P - 1 - aend;
           const T* dN = g.tab[d] + jl * O::stride + (side ? O::dL : O::dR);
           const double* un = u + (long long)nb * P3 + base;
+          double r[P + 2];  // all loads issued before the conversions
+#pragma unroll
+          for (int a = 0; a < P; ++a) r[a] = __ldg(un + d * N + a * sd);
+          r[P] = __ldg(un + ta * N + nend * sd);
+          r[P + 1] = __ldg(un + tb * N + nend * sd);
           T g_nb = T(0);
 #pragma unroll
-          for (int a = 0; a < P; ++a) g_nb = fma(dN[a], cvt_in<T, double>(un[d * N + a * sd], xsc), g_nb);
-          const T udn = cvt_in<T, double>(un[d * N + nend * sd], xsc);
-          const T uan = cvt_in<T, double>(un[ta * N + nend * sd], xsc);
-          const T ubn = cvt_in<T, double>(un[tb * N + nend * sd], xsc);
+          for (int a = 0; a < P; ++a) g_nb = fma(dN[a], cvt_in<T, double>(r[a], xsc), g_nb);
+          const T udn = cvt_in<T, double>(nend ? r[P - 1] : r[0], xsc);
+          const T uan = cvt_in<T, double>(r[P], xsc);
+          const T ubn = cvt_in<T, double>(r[P + 1], xsc);
           avgN = T(0.5) * (g_own + g_nb);
           avgU = T(0.5) * (ud + udn);
           Jd = ud - udn;

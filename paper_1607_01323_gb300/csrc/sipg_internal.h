@@ -84,6 +84,8 @@ struct Geo {
   const T* tab[3];  // per-direction layer tables on the device
   T tau_scale;      // penalty factor * (k+1)^2
   const int* dsc;   // scale exponent of the call (double-float kernels; see launch_df_scale)
+  int lm[3];        // layer-index mask of the uniform operator: 0 where every layer of the
+                    // direction has the same table (all cells read layer 0's copy), else -1
 };
 
 // Host-side state of one mesh.
@@ -128,6 +130,7 @@ struct Mesh {
   bool general() const { return desc.map == SIPG_MAP_PERTURBED; }
   bool eo_xz = false;  // every x- and z-layer centrosymmetric (even-odd contractions, p >= 5)
   int f64_arith = 0;  // FP64 operator arithmetic: 0 native FP64, 1 double-float
+  int lay_same[3] = {0, 0, 0};  // every layer of the direction has a bitwise equal table
   int f32_mapping = 0;  // FP32 uniform operator: 0 one line per thread, 1 one plane per thread
   int cpb[2] = {0, 0};  // cells per block, [0] FP64, [1] FP32 (0 = default)
   int cpb_conv = 0;     // cells per block of the convective kernel (0 = default)

@@ -362,6 +362,13 @@ int build_tables(Mesh& m) {
       tab[(size_t)i * st + lay_dTR(p)] = tr > ts ? tr - ts : 0.0;
     }
   }
+  // directions whose layers all have the same table (equal widths of an
+  // affine direction: the tables depend on the local nodes only)
+  for (int dir = 0; dir < 3; ++dir) {
+    m.lay_same[dir] = 1;
+    for (int i = 1; i < m.desc.n[dir] && m.lay_same[dir]; ++i)
+      if (std::memcmp(&m.htab[dir][(size_t)i * st], &m.htab[dir][0], st * sizeof(double)) != 0) m.lay_same[dir] = 0;
+  }
   // even-odd contractions along x and z when all their layers allow it
   m.eo_xz = p >= 5;
   for (int dir : {0, 2})
