@@ -386,12 +386,24 @@ __global__ void divdiv_solve_kernel(Geo<T> g, const T* __restrict__ Cg, const do
   // products only enter ratios
   const int sc = call_scale(g);
   double bb = 0.0;
-  for (int i = threadIdx.x; i < V; i += blockDim.x) {
-    const long long gi = (i / P3) * N + (long long)e * P3 + i % P3;
-    sx[i] = cvt_in<T, double>(x[gi], sc);
-    const double b = rhs[gi];
-    sr[i] = cvt_in<T, double>(b, sc);
-    bb += b * b;
+  for (int i0 = threadIdx.x; i0 < V; i0 += 2 * blockDim.x) {
+    double xv[2], bv[2];  // the loads of two entries issued before their conversions
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int i = i0 + j * blockDim.x;
+      const long long gi = (i / P3) * N + (long long)e * P3 + i % P3;
+      xv[j] = i < V ? __ldg(x + gi) : 0.0;
+      bv[j] = i < V ? __ldg(rhs + gi) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int i = i0 + j * blockDim.x;
+      if (i < V) {
+        sx[i] = cvt_in<T, double>(xv[j], sc);
+        sr[i] = cvt_in<T, double>(bv[j], sc);
+        bb += bv[j] * bv[j];
+      }
+    }
   }
   stage_c<P>(Cg, C, Ct);
   const CellCtxT<T> cc = cell_ctx<P>(g, e, (const T*)C, (const T*)Ct);
