@@ -748,14 +748,27 @@ __host__ __device__ constexpr size_t uniform_smem_bytes(int cpb) {
   return (size_t)3 * cpb * P * P * P * sizeof(T);
 }
 
+// The layer tables of the x and z directions passed by value in the kernel's
+// parameter space, for a mesh whose x-layers all share one table and whose
+// z-layers do too (uniform spacing; Mesh::lay_same): the contractions then
+// read their entries as constant-bank operands instead of issuing loads.
+template <typename T, int P>
+struct __align__(16) XZTab {
+  T x[LayerOff<P>::stride];
+  T z[LayerOff<P>::stride];
+};
+struct NoXZTab {};
+
 // CHEB (FP32 only): instead of storing y = A x, apply one Chebyshev step of the
 // multigrid smoother to the block's own unknowns with x = d (see ChebEpi).
 // EOXZ: every x- and z-layer of the mesh is centrosymmetric (Mesh::eo_xz):
 // their contractions take the even-odd form (p >= 5).
-template <typename T, typename S, int P, bool CHEB = false, bool EOXZ = false>
+// PXZ: the x and z tables come in xz (XZTab) instead of g.tab[0], g.tab[2].
+template <typename T, typename S, int P, bool CHEB = false, bool EOXZ = false, bool PXZ = false>
 __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value)
     apply_uniform_kernel(Geo<T> g, const S* __restrict__ x, S* __restrict__ y, int cpb, T mass_rel, T scale,
-                         int do_scale, int do_mass, DotSink sink, ChebEpi epi) {
+                         int do_scale, int do_mass, DotSink sink, ChebEpi epi,
+                         const __grid_constant__ std::conditional_t<PXZ, XZTab<T, P>, NoXZTab> xz) {
   if (sink.skip && *sink.skip) return;
   double* dots = sink.partials;
   using O = LayerOff<P>;
@@ -780,6 +793,14 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     stage_cvt<T, S>(su, xb, nc * P3, sc);
   }
   __syncthreads();
+  // the table of `layer` along direction dir
+  auto tab = [&](int dir, int layer) -> const T* {
+    if constexpr (PXZ) {
+      if (dir == 0) return xz.x;
+      if (dir == 2) return xz.z;
+    }
+    return g.tab[dir] + (layer & g.lm[dir]) * O::stride;
+  };
   T* us = su + cs * P3;
   T* v1 = s1 + cs * P3;
   T* v2 = s2 + cs * P3;
@@ -789,8 +810,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     id[0] = e % g.n[0];
     id[1] = (e / g.n[0]) % g.n[1];
     id[2] = e / (g.n[0] * g.n[1]);
-    tau_e = g.tab[0][(id[0] & g.lm[0]) * O::stride + O::ts] + g.tab[1][(id[1] & g.lm[1]) * O::stride + O::ts] +
-            g.tab[2][(id[2] & g.lm[2]) * O::stride + O::ts];
+    tau_e = tab(0, id[0])[O::ts] + tab(1, id[1])[O::ts] + tab(2, id[2])[O::ts];
   }
   const T tau2e = tau_e + tau_e;
   if (active) {
@@ -799,7 +819,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     for (int dir = 0; dir < 2; ++dir) {
       int start, step;
       line_geom<P>(dir, ti, tj, start, step);
-      const T* L = g.tab[dir] + (id[dir] & g.lm[dir]) * O::stride;
+      const T* L = tab(dir, id[dir]);
       int nbL, nbR, kL, kR, jl, jr;
       face_neighbor(g, dir, 0, id[dir], e, nbL, kL, jl);
       face_neighbor(g, dir, 1, id[dir], e, nbR, kR, jr);
@@ -821,8 +841,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
         else
           load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
       }
-      line_op_q<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[dir] + (jl & g.lm[dir]) * O::stride : L, tau_e + L[O::dTL], kR, uR,
-                      kR == 0 ? g.tab[dir] + (jr & g.lm[dir]) * O::stride : L, tau_e + L[O::dTR], tau2e, dir == 0 && EOX);
+      line_op_q<T, P>(w, u, L, kL, uL, kL == 0 ? tab(dir, jl) : L, tau_e + L[O::dTL], kR, uR,
+                      kR == 0 ? tab(dir, jr) : L, tau_e + L[O::dTR], tau2e, dir == 0 && EOX);
       store_line<T, P>(dir == 0 ? v1 : v2, w, start, step);
     }
   }
@@ -831,7 +851,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     // phase Z on the z-lines: Mz (V1 + V2 + mass_rel u) + w_z -> V1
     int start, step;
     line_geom<P>(2, ti, tj, start, step);
-    const T* L = g.tab[2] + (id[2] & g.lm[2]) * O::stride;
+    const T* L = tab(2, id[2]);
     constexpr bool eoz = EOX;
     int nbL, nbR, kL, kR, jl, jr;
     face_neighbor(g, 2, 0, id[2], e, nbL, kL, jl);
@@ -840,8 +860,8 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     load_line<T, P>(u, us, start, step);
     if (kL == 0) load_line_global_cvt<T, S, P>(uL, xc + (long long)nbL * P3, start, step, sc);
     if (kR == 0) load_line_global_cvt<T, S, P>(uR, xc + (long long)nbR * P3, start, step, sc);
-    line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? g.tab[2] + (jl & g.lm[2]) * O::stride : L, tau_e + L[O::dTL], kR, uR,
-                    kR == 0 ? g.tab[2] + (jr & g.lm[2]) * O::stride : L, tau_e + L[O::dTR], tau2e, eoz);
+    line_op_u<T, P>(w, u, L, kL, uL, kL == 0 ? tab(2, jl) : L, tau_e + L[O::dTL], kR, uR,
+                    kR == 0 ? tab(2, jr) : L, tau_e + L[O::dTR], tau2e, eoz);
     T v[P], r[P];
     load_line<T, P>(v, v1, start, step);
     {
@@ -866,7 +886,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     line_geom<P>(1, ti, tj, start, step);
     T v[P], r[P];
     load_line<T, P>(v, v1, start, step);
-    const T* Ly = g.tab[1] + (id[1] & g.lm[1]) * O::stride;
+    const T* Ly = tab(1, id[1]);
     matvec_l<T, P>(r, Ly, O::M, O::EM, false, v);
     store_line<T, P>(v1, r, start, step);
   }
@@ -879,7 +899,7 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
     line_geom<P>(0, ti, tj, start, step);
     T v[P], out[P];
     load_line<T, P>(v, v1, start, step);
-    const T* Lx = g.tab[0] + (id[0] & g.lm[0]) * O::stride;
+    const T* Lx = tab(0, id[0]);
     matvec_l<T, P>(out, Lx, O::M, O::EM, EOX, v);
 #pragma unroll
     for (int a = 0; a < P; ++a)

@@ -9,20 +9,43 @@
 namespace sipg {
 
 // Launch of apply_uniform_kernel, with the even-odd x/z contractions when the
-// mesh allows them (p >= 5, Mesh::eo_xz).
+// mesh allows them (p >= 5, Mesh::eo_xz) and, in FP32 and double-float, the x
+// and z tables as kernel parameters when each of the two directions has one
+// table for all its layers (the FP64 kernel is bound by its FP64 pipe, not
+// by its loads).
 template <typename T, typename S, int P, bool CHEB>
 static cudaError_t launch_uniform(const Mesh& m, dim3 grid, int threads, size_t smem, cudaStream_t s, const Geo<T>& g,
                                   const S* x, S* y, int cpb, T mass_rel, T scale, int do_scale, int do_mass,
                                   const DotSink& ds, const ChebEpi& epi) {
-  auto k = apply_uniform_kernel<T, S, P, CHEB, false>;
-  if constexpr (P >= 5) {
-    if (m.eo_xz) k = apply_uniform_kernel<T, S, P, CHEB, true>;
+  const bool big = smem + 2048 > 48 * 1024;  // dynamic + static shared memory above the default limit
+  if constexpr (!std::is_same<T, double>::value) {
+    if (m.lay_same[0] && m.lay_same[2]) {
+      XZTab<T, P> xz;
+      for (int j = 0; j < LayerOff<P>::stride; ++j) {
+        xz.x[j] = T(m.htab[0][j]);  // the same conversion as the device tables'
+        xz.z[j] = T(m.htab[2][j]);
+      }
+      auto k = apply_uniform_kernel<T, S, P, CHEB, false, true>;
+      if constexpr (P >= 5) {
+        if (m.eo_xz) k = apply_uniform_kernel<T, S, P, CHEB, true, true>;
+      }
+      if (big) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      k<<<grid, threads, smem, s>>>(g, x, y, cpb, mass_rel, scale, do_scale, do_mass, ds, epi, xz);
+      return cudaGetLastError();
+    }
   }
-  if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
+  auto k = apply_uniform_kernel<T, S, P, CHEB, false, false>;
+  if constexpr (P >= 5) {
+    if (m.eo_xz) k = apply_uniform_kernel<T, S, P, CHEB, true, false>;
+  }
+  if (big) {
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k<<<grid, threads, smem, s>>>(g, x, y, cpb, mass_rel, scale, do_scale, do_mass, ds, epi);
+  k<<<grid, threads, smem, s>>>(g, x, y, cpb, mass_rel, scale, do_scale, do_mass, ds, epi, NoXZTab());
   return cudaGetLastError();
 }
 
