@@ -933,20 +933,35 @@ __global__ void __launch_bounds__(kMaxCellThreads, UniformMinBlocks<T, P>::value
   // the block's cells are contiguous in memory: consecutive threads write
   // (or, for the Chebyshev step, update) consecutive entries
   const long long o0 = cbase + cell0 * P3;
-  for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) {
-    const T tv = s2[idx];
-    if constexpr (CHEB) {
-      static_assert(std::is_same<T, float>::value && std::is_same<S, float>::value, "FP32 only");
-      // r -= A d, dnew = c1 d + c2 D^-1 r, x += dnew with d the staged input
-      const long long o = o0 + idx;
-      const float ri = epi.r[o] - tv;
-      const float di = epi.c1 * su[idx] + epi.c2 * ri * epi.dinv[o];
-      epi.r[o] = ri;
-      epi.dnew[o] = di;
-      epi.x[o] += di;
-    } else {
-      y[o0 + idx] = cvt_out<S, T>(tv, sc);
+  if constexpr (CHEB) {
+    static_assert(std::is_same<T, float>::value && std::is_same<S, float>::value, "FP32 only");
+    // r -= A d, dnew = c1 d + c2 D^-1 r, x += dnew with d the staged input;
+    // each thread loads r, D^-1 and x of four entries before it updates them
+    // (the stores of one entry could otherwise hold back the next one's loads)
+    const int n = nc * P3, bd = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < n; i0 += 4 * bd) {
+      float rv[4], dv[4], xv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = i0 + j * bd;
+        rv[j] = i < n ? epi.r[o0 + i] : 0.f;
+        dv[j] = i < n ? epi.dinv[o0 + i] : 0.f;
+        xv[j] = i < n ? epi.x[o0 + i] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = i0 + j * bd;
+        if (i < n) {
+          const float ri = rv[j] - s2[i];
+          const float di = epi.c1 * su[i] + epi.c2 * ri * dv[j];
+          epi.r[o0 + i] = ri;
+          epi.dnew[o0 + i] = di;
+          epi.x[o0 + i] = xv[j] + di;
+        }
+      }
     }
+  } else {
+    for (int idx = threadIdx.x; idx < nc * P3; idx += blockDim.x) y[o0 + idx] = cvt_out<S, T>(s2[idx], sc);
   }
 }
 
