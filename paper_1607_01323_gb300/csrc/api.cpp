@@ -400,7 +400,7 @@ int sipg_apply_inverse_mass_f64(const sipg_mesh* mc, const double* x, double* y,
   if ((st = check_vec(x, y, ncomp))) return st;
   Mesh& m = const_cast<sipg_mesh&>(*mc);
   if ((st = set_device(m))) return st;
-  return launch_inverse_mass(m, x, y, ncomp, nullptr, nullptr, (cudaStream_t)stream);
+  return launch_inverse_mass(m, x, y, ncomp, nullptr, false, (cudaStream_t)stream);
 }
 
 int sipg_diagonal_f64(const sipg_mesh* mc, int op, double cm, double nu, const double* nu_cell, double* diag,
@@ -589,7 +589,8 @@ int sipg_apply_viscous_f64(const sipg_mesh* m, double mass_coef, double nu, cons
   if ((st = set_device(*m))) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = launch_apply<double>(*m, u, y, 3, mass_coef, nu, nullptr, true, nullptr, nullptr, s))) return st;
-  return launch_viscous_t(*m, u, y, nu, nullptr, s);
+  // in double-float the operator's scale pass over u left u's scale in the mesh's word
+  return launch_viscous_t(*m, u, y, nu, nullptr, m->f64_arith == SIPG_F64_DOUBLE_FLOAT, s);
 }
 
 int sipg_apply_convective_f64(const sipg_mesh* m, const double* u, double* y, void* stream) {

@@ -255,10 +255,13 @@ __global__ void k_init_precond(const Scalars* __restrict__ sc, long long n, doub
 //    otherwise (separate preconditioner) it leaves (r.r) partials for k_beta.
 // Every FP64 operation counts on this GPU (2 FP64 FMA/clk/SM): the mean
 // subtraction and z.q are compiled out when not needed.
+// With a separate preconditioner and rsc set, it also reduces the
+// double-float scale of the new r into the mesh's word (see k_pupdate), so
+// that a double-float M^-1 skips its scale pass.
 template <bool FORM_Z, bool ZERO_MEAN, bool ZQ>
 __global__ void k_update(Scalars* sc, long long n, double* __restrict__ x, double* r, const double* __restrict__ p,
                          const double* __restrict__ ap, double* z, const double* __restrict__ diag,
-                         double* __restrict__ part, int flexible) {
+                         double* __restrict__ part, int flexible, int* __restrict__ rsc) {
   if (sc->done) return;
   const double mean = ZERO_MEAN ? sc->tot[1] / sc->ntot : 0.0;
   const double pap = sc->tot[0] - mean * sc->tot[2];
@@ -274,11 +277,13 @@ __global__ void k_update(Scalars* sc, long long n, double* __restrict__ x, doubl
   // accesses) when the vectors are 16-byte aligned and n is even.
   float rr32 = 0.f;
   double rz = 0.0, zq = 0.0;
+  int rkey = 0;  // largest double-float scale key of r (rsc only)
   auto one = [&](long long i) {
     const double q = ZERO_MEAN ? ap[i] - mean : ap[i];
     x[i] = fma(alpha, p[i], x[i]);
     const double ri = fma(-alpha, q, r[i]);
     r[i] = ri;
+    if (!FORM_Z && rsc) rkey = max(rkey, df_scale_key(ri));
     const float rf = f64_top24(ri);
     rr32 = fmaf(rf, rf, rr32);
     if (FORM_Z) {
@@ -303,6 +308,7 @@ __global__ void k_update(Scalars* sc, long long n, double* __restrict__ x, doubl
       const double r0 = fma(-alpha, q0, rv.x), r1 = fma(-alpha, q1, rv.y);
       reinterpret_cast<double2*>(x)[j] = make_double2(fma(alpha, pv.x, xv.x), fma(alpha, pv.y, xv.y));
       reinterpret_cast<double2*>(r)[j] = make_double2(r0, r1);
+      if (!FORM_Z && rsc) rkey = max(rkey, max(df_scale_key(r0), df_scale_key(r1)));
       const float f0 = f64_top24(r0), f1 = f64_top24(r1);
       rr32 = fmaf(f0, f0, fmaf(f1, f1, rr32));
       if (FORM_Z) {
@@ -316,6 +322,7 @@ __global__ void k_update(Scalars* sc, long long n, double* __restrict__ x, doubl
     for (long long i = t0; i < n; i += stride) one(i);
   }
   block_partial_update<ZQ>(rr32, rz, zq, part);
+  if (!FORM_Z && rsc) df_scale_reduce(rkey, rsc);
   if (!FORM_Z) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       sc->alpha = alpha;
@@ -365,7 +372,7 @@ __global__ void k_update(Scalars* sc, long long n, double* __restrict__ x, doubl
 }
 
 using UpdateFn = void (*)(Scalars*, long long, double*, double*, const double*, const double*, double*,
-                          const double*, double*, int);
+                          const double*, double*, int, int*);
 
 UpdateFn pick_update(bool form_z, bool zero_mean, bool zq) {
   if (!form_z) return zero_mean ? k_update<false, true, false> : k_update<false, false, false>;
@@ -693,10 +700,14 @@ struct Solver {
   }
 
   // the search direction's double-float scale comes from k_pupdate (operators
-  // of the separable kernels only; the others run their own scale pass)
+  // of the separable kernels only; the general-map kernel runs its own scale
+  // pass)
   int* pscale() const {
-    return (m.f64_arith == SIPG_F64_DOUBLE_FLOAT && !visc && !m.general()) ? m.dscale : nullptr;
+    return (m.f64_arith == SIPG_F64_DOUBLE_FLOAT && !m.general()) ? m.dscale : nullptr;
   }
+  // the residual's scale comes from k_update when the double-float M^-1
+  // preconditions it
+  int* rscale() const { return (o.precond == SIPG_PC_INVMASS && pscale()) ? m.dscale : nullptr; }
 
   int apply64(const double* x, double* y, double* dots, int* nb) {
     DotSink sink;
@@ -724,8 +735,12 @@ struct Solver {
       // the transposed-gradient coupling, then the dot products p.Ap
       DotSink skip_only;
       skip_only.skip = dots ? &w.sc->done : nullptr;
+      skip_only.prescaled = sink.prescaled;
       st = launch_apply<double>(m, x, y, ncomp, cm, nu, nullptr, true, &skip_only, nullptr, s);
-      if (!st) st = launch_viscous_t(m, x, y, nu, dots ? &w.sc->done : nullptr, s);
+      // in double-float, x's scale is in the mesh's word by now (from k_pupdate
+      // or from the operator's own scale pass)
+      if (!st)
+        st = launch_viscous_t(m, x, y, nu, dots ? &w.sc->done : nullptr, m.f64_arith == SIPG_F64_DOUBLE_FLOAT, s);
       if (!st && dots) {
         k_dot_sink<<<kVecBlocks, kVecThreads, 0, s>>>(&w.sc->done, n, x, y, dots, &w.sc->cnt_apply, w.sc->tot, 0);
         st = launched();
@@ -805,11 +820,12 @@ struct Solver {
     double* z = (o.precond == SIPG_PC_NONE) ? w.r : w.z;
     const int flex = fp32_precond() || (o.flexible && o.precond != SIPG_PC_INVMASS);
     pick_update(!sep, o.zero_mean != 0, flex != 0)<<<kVecBlocks, kVecThreads, 0, s>>>(w.sc, n, xcur, w.r, w.p, w.ap,
-                                                                                      z, dg, w.part1, flex);
+                                                                                      z, dg, w.part1, flex,
+                                                                                      sep ? rscale() : nullptr);
     if ((st = launched())) return st;
     int nb2 = kVecBlocks;
     if (o.precond == SIPG_PC_INVMASS) {
-      if ((st = launch_inverse_mass(m, w.r, w.z, ncomp, w.part2, nullptr, s))) return st;
+      if ((st = launch_inverse_mass(m, w.r, w.z, ncomp, w.part2, rscale() != nullptr, s))) return st;
       nb2 = (int)(((m.ncell + (m.cpb[0] > 0 ? m.cpb[0] : default_cpb(m.p, 0)) - 1) /
                    (m.cpb[0] > 0 ? m.cpb[0] : default_cpb(m.p, 0))) *
                   ncomp);
@@ -870,7 +886,7 @@ struct Solver {
     if (sep) {
       int nb2 = kVecBlocks;
       if (o.precond == SIPG_PC_INVMASS) {
-        if ((st = launch_inverse_mass(m, w.r, w.z, ncomp, w.part2, nullptr, s))) return st;
+        if ((st = launch_inverse_mass(m, w.r, w.z, ncomp, w.part2, false, s))) return st;
         const int cpb = m.cpb[0] > 0 ? m.cpb[0] : default_cpb(m.p, 0);
         nb2 = (int)(((m.ncell + cpb - 1) / cpb) * ncomp);
       } else if (o.precond == SIPG_PC_GMG_F32) {

@@ -26,7 +26,8 @@ __global__ void __launch_bounds__(kScaleThreads) df_scale_kernel(const double* _
 }
 
 template <int P>
-int launch_inverse_mass_p(const Mesh& m, const double* x, double* y, int ncomp, double* dots, cudaStream_t s) {
+int launch_inverse_mass_p(const Mesh& m, const double* x, double* y, int ncomp, double* dots, bool prescaled,
+                          cudaStream_t s) {
   const int cpb = m.cpb[0] > 0 ? m.cpb[0] : default_cpb(P, 0);
   const dim3 grid((unsigned)((m.ncell + cpb - 1) / cpb), (unsigned)ncomp);
   const size_t smem = (size_t)cpb * P * P * P * sizeof(double);
@@ -34,8 +35,10 @@ int launch_inverse_mass_p(const Mesh& m, const double* x, double* y, int ncomp, 
   if (threads > kMaxCellThreads) return fail(SIPG_EINVAL, "cells per block too large for this degree");
   // same arithmetic choice as the operator (double-float keeps FP64 data)
   if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
-    const int st = launch_df_scale(m, x, m.ncell * P * P * P * ncomp, nullptr, 0, nullptr, s);
-    if (st) return st;
+    if (!prescaled) {
+      const int st = launch_df_scale(m, x, m.ncell * P * P * P * ncomp, nullptr, 0, nullptr, s);
+      if (st) return st;
+    }
     if (smem + 2048 > 48 * 1024) {  // dynamic + static shared memory above the default limit
       cudaError_t e = cudaFuncSetAttribute(inverse_mass_kernel<dfl, double, P>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -99,9 +102,9 @@ bool df_coef_ok(double v) {
     default: return fail(SIPG_EINVAL, "unsupported degree"); \
   }
 
-int launch_inverse_mass(const Mesh& m, const double* x, double* y, int ncomp, double* dots, const double*,
+int launch_inverse_mass(const Mesh& m, const double* x, double* y, int ncomp, double* dots, bool prescaled,
                         cudaStream_t s) {
-  SIPG_DISPATCH_P(launch_inverse_mass_p, m, x, y, ncomp, dots, s)
+  SIPG_DISPATCH_P(launch_inverse_mass_p, m, x, y, ncomp, dots, prescaled, s)
 }
 
 int launch_diagonal(const Mesh& m, bool stiffness, double cm, double nu, const double* nu_cell, double* diag,

@@ -729,7 +729,8 @@ int launch_divdiv_solve_p(const Mesh& m, const double* tau, const double* rhs, d
 }
 
 template <int P>
-int launch_viscous_t_p(const Mesh& m, const double* u, double* y, double scale, const int* skip, cudaStream_t s) {
+int launch_viscous_t_p(const Mesh& m, const double* u, double* y, double scale, const int* skip, bool prescaled,
+                       cudaStream_t s) {
   constexpr int P3 = P * P * P;
   const size_t smem = (size_t)(8 * P3 + 2 * P * P + 11 * P * P) * sizeof(double);
   cudaError_t e;
@@ -742,8 +743,10 @@ int launch_viscous_t_p(const Mesh& m, const double* u, double* y, double scale, 
   }
   if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT) {
     if (!df_coef_ok(scale)) return fail(SIPG_EINVAL, "double-float arithmetic needs nu in [2^-100, 2^100]");
-    const int st = launch_df_scale(m, u, 3 * m.ncell * P3, nullptr, 0, skip, s);
-    if (st) return st;
+    if (!prescaled) {
+      const int st = launch_df_scale(m, u, 3 * m.ncell * P3, nullptr, 0, skip, s);
+      if (st) return st;
+    }
   }
   if (m.f64_arith == SIPG_F64_DOUBLE_FLOAT)
     viscous_t_kernel<dfl, P><<<(unsigned)m.ncell, cell_threads(P), smem, s>>>(make_geo<dfl>(m), m.dCdf, u, y, scale,
@@ -794,8 +797,9 @@ int launch_divdiv_apply(const Mesh& m, const double* tau, const double* u, doubl
 #undef CALL
 }
 
-int launch_viscous_t(const Mesh& m, const double* u, double* y, double scale, const int* skip, cudaStream_t s) {
-#define CALL(P) launch_viscous_t_p<P>(m, u, y, scale, skip, s)
+int launch_viscous_t(const Mesh& m, const double* u, double* y, double scale, const int* skip, bool prescaled,
+                     cudaStream_t s) {
+#define CALL(P) launch_viscous_t_p<P>(m, u, y, scale, skip, prescaled, s)
   SIPG_PROJ_DISPATCH(CALL)
 #undef CALL
 }

@@ -232,7 +232,9 @@ int launch_df_scale(const Mesh& m, const double* v, long long n, const double* v
 // [2^-100, 2^100] in magnitude (the FP32 exponent range with room to spare).
 bool df_coef_ok(double v);
 
-int launch_inverse_mass(const Mesh& m, const double* x, double* y, int ncomp, double* dots, const double* rdot,
+// prescaled: x's double-float scale is already in the mesh's word (set by the
+// kernel that wrote x), so the scale pass is skipped
+int launch_inverse_mass(const Mesh& m, const double* x, double* y, int ncomp, double* dots, bool prescaled,
                         cudaStream_t s);
 int launch_diagonal(const Mesh& m, bool stiffness, double mass_coef, double nu, const double* nu_cell, double* diag,
                     cudaStream_t s);
@@ -260,7 +262,8 @@ int convective_cpb(const Mesh& m, int* max_cpb);
 // y += scale * T u, the transposed-gradient part of the divergence-form
 // viscous operator (3 components in and out; projection.cu); returns at once
 // when skip is set and *skip != 0
-int launch_viscous_t(const Mesh& m, const double* u, double* y, double scale, const int* skip, cudaStream_t s);
+int launch_viscous_t(const Mesh& m, const double* u, double* y, double scale, const int* skip, bool prescaled,
+                     cudaStream_t s);
 
 int cg_solve_noalloc(Mesh& m, const sipg_cg_opts& o, const double* b, double* x, int ncomp, cudaStream_t s,
                      int* iters, double* relres);
